@@ -1,0 +1,59 @@
+"""Plausible mistakes planted in copies of the oracle must fail a pin.
+
+Each mutant is a textual edit of ``oracle/qsim_oracle.c`` compiled on the CPU
+into a temporary library; the pins of ``oracle_pins.py`` run against it and
+at least one of them must fail.
+"""
+
+import os
+
+import pytest
+
+import oracle
+from oracle_pins import PINS
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "qsim_oracle.c")
+
+MUTANTS = {
+    "transposed_U": [("psi[i] = u00 * a + u01 * b;", "psi[i] = u00 * a + u10 * b;"),
+                     ("psi[j] = u10 * a + u11 * b;", "psi[j] = u01 * a + u11 * b;")],
+    "dropped_term": [("psi[j] = u10 * a + u11 * b;", "psi[j] = u11 * b;")],
+    "controls_ignored": [("if ((i & ctl_mask) != ctl_mask) continue;", "")],
+    "control_inverted": [("if ((i & ctl_mask) != ctl_mask) continue;",
+                          "if (ctl_mask && (i & ctl_mask) == ctl_mask) continue;")],
+    "imag_sign_U": [("u01 = U[2] + I * U[3];", "u01 = U[2] - I * U[3];")],
+    "pair_index": [("uint64_t j = i | tbit;", "uint64_t j = i ^ (tbit >> 1);")],
+    "overlap_no_conj": [("s += conj(a[i]) * b[i];", "s += a[i] * b[i];")],
+    "norm_drops_imag": [("s += creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);",
+                         "s += creal(psi[i]) * creal(psi[i]);")],
+    "error_axis_sign": [("const cplx e01 = -I * s * (nx - I * ny);",
+                         "const cplx e01 = -I * s * (nx + I * ny);")],
+    "error_half_angle": [("const double c = cos(0.5 * eps), s = sin(0.5 * eps);",
+                          "const double c = cos(eps), s = sin(eps);")],
+    "error_left_multiply": [("const cplx r00 = u00 * e00 + u01 * e10, r01 = u00 * e01 + u01 * e11;",
+                             "const cplx r00 = e00 * u00 + e01 * u10, r01 = e00 * u01 + e01 * u11;"),
+                            ("const cplx r10 = u10 * e00 + u11 * e10, r11 = u10 * e01 + u11 * e11;",
+                             "const cplx r10 = e10 * u00 + e11 * u10, r11 = e10 * u01 + e11 * u11;")],
+    "variance_biased": [("*var = (T > 1) ? v / (T - 1) : 0.0;", "*var = v / T;")],
+    "probability_amplitude": [("p[i] = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);",
+                               "p[i] = creal(psi[i]) + cimag(psi[i]);")],
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    src = open(SRC).read()
+    for old, new in MUTANTS[name]:
+        assert old in src, (name, old)
+        src = src.replace(old, new)
+    path = tmp_path / f"{name}.c"
+    path.write_text(src)
+    lib = oracle.compile_oracle(str(path), str(tmp_path / f"lib{name}.so"))
+    mut = oracle.Oracle(oracle.load(lib))
+    failed = []
+    for pin in PINS:
+        try:
+            pin(mut)
+        except (AssertionError, ValueError):
+            failed.append(pin.__name__)
+    assert failed, f"mutant {name} passed every pin"
