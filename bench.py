@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the error-injecting state-vector simulator on GB300.
+
+Workload (default): the quantum-FFT circuit on M=28 qubits, complex64
+(2 GiB per state vector): H + controlled-R_k ladder (406 gates) + 14
+bit-reversal swaps, Gaussian phase error sigma=1e-4 per gate, applied to a
+random normalised complex Gaussian input.  One step = the error-free circuit
+and the noisy circuit, both from the resident input state, then the fidelity
+|<ideal|noisy>|^2 and the noisy norm read back to the host.
+
+metric: amplitude-updates/s = (logical gates applied) * 2^M / second, summed
+over ranks.  Per-launch CUDA events (recorded by the library on the launching
+stream inside the timed region) give the dominant kernel's roofline figures.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (no collective
+on the data path: the per-rank work is fixed, weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "qft-m28-c64": dict(M=28, sigma=1e-4),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="qft-m28-c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="tiled", choices=["auto", "tiled", "unfused", "fused"])
+    ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ ranks ---
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, local):
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ cpu baseline ---
+def oracle_sample(M, gates, x, budget_s: float, min_gates: int = 3):
+    """Time the CPU oracle (all host threads) on the first gates of the noisy
+    circuit at the full size M, for about budget_s seconds.  Returns
+    (amp-updates/s, gates applied, seconds, threads)."""
+    import oracle
+    orc = oracle.Oracle()
+    nt = oracle.default_threads()
+    psi = x.astype(np.complex128)
+    t0 = time.perf_counter()
+    n = 0
+    while n < len(gates) and (n < min_gates or time.perf_counter() - t0 < budget_s):
+        orc.apply_circuit(psi, gates[n:n + 1], nthreads=nt)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n * float(1 << M) / dt, n, dt, nt
+
+
+# ---------------------------------------------------------------- ours ---
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_quant_ph_9804039_gb300 as qs
+    from workloads import generators as W
+
+    wl = WORKLOADS[args.workload]
+    M = wl["M"]
+    c = W.circuit_c2_qft(M, sigma=wl["sigma"])
+    n_logical = c["n_logical_gates"]
+    x = W.random_state(M, seed=2)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    xin = qs.State(M, device=dev, stream=stream, zero=False).set(x)
+    ideal = qs.State(M, device=dev, stream=stream, zero=False)
+    noisy = qs.State(M, device=dev, stream=stream, zero=False)
+    mode = args.mode
+    p_ideal = qs.Plan(M, c["ideal"], mode=mode, tile_bits=args.tile_bits)
+    p_noisy = qs.Plan(M, c["noisy"], mode=mode, tile_bits=args.tile_bits)
+    st_i, st_n = p_ideal.stats(), p_noisy.stats()
+    amp_updates_step = 2.0 * n_logical * float(1 << M)
+    launches_step = st_i["n_launches"] + st_n["n_launches"] + 2
+
+    def step():
+        p_ideal.execute(ideal, xin)
+        p_noisy.execute(noisy, xin)
+        return qs.fidelity(ideal, noisy)
+
+    for _ in range(args.warmup):
+        F, nrm = step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    p_ideal.set_timing(True)
+    p_noisy.set_timing(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            F, nrm = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    p_ideal.set_timing(False)
+    p_noisy.set_timing(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = amp_updates_step * world / (ms / 1e3)
+
+    # dominant kernel: per-launch event times of both plans
+    kinds = {}
+    for p in (p_ideal, p_noisy):
+        t_ms, t_bytes, t_kind, execs = p.timing()
+        for j in range(len(t_ms)):
+            k = int(t_kind[j])
+            d = kinds.setdefault(k, [0.0, 0.0, 0])
+            d[0] += t_ms[j]
+            d[1] += t_bytes[j] * execs
+            d[2] += execs
+    kname = {0: "k_gate (one gate per launch)", 1: "k_tile_pass", 2: "k_fused_tc"}
+    top = max(kinds, key=lambda k: kinds[k][0])
+    tot_ms, tot_bytes, n_launch = kinds[top]
+    peak, peak_src = measured_peaks()
+    achieved = tot_bytes / (tot_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname[top], "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "launches_timed": n_launch,
+                "avg_launch_ms": round(tot_ms / max(1, n_launch), 4),
+                "kernel_share_of_step": round(tot_ms / (ms * args.steps), 4)}
+
+    result = {
+        "metric": "amplitude-updates/s", "value": value, "unit": "amp-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+        "config": {"workload": args.workload, "M": M, "circuit": "qft", "sigma": wl["sigma"],
+                   "gates_per_circuit": n_logical, "gate_records_per_circuit": int(len(c["noisy"])),
+                   "circuits_per_step": 2, "mode": mode, "tile_bits": st_n["tile_bits"],
+                   "passes_per_circuit": st_n["n_passes"], "l2": "inputs larger than L2 (2 GiB per state)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roofline,
+        "gpu_launches": int(launches_step * args.steps),
+        "fidelity": F, "norm": nrm,
+        "hbm_gbs_step": (st_i["algo_bytes"] + st_n["algo_bytes"] + 2 * 8 * float(1 << M)) / (ms / 1e3) / 1e9,
+    }
+    result["clocks"] = clk.summary()
+
+    # one-gate-per-launch form on the same GPU
+    if not args.no_unfused and mode != "unfused":
+        pu_i = qs.Plan(M, c["ideal"], mode="unfused")
+        pu_n = qs.Plan(M, c["noisy"], mode="unfused")
+        ku = max(1, min(args.steps, 3))
+        pu_i.execute(ideal, xin)
+        pu_n.execute(noisy, xin)
+        qs.fidelity(ideal, noisy)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ku):
+            pu_i.execute(ideal, xin)
+            pu_n.execute(noisy, xin)
+            Fu, _ = qs.fidelity(ideal, noisy)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msu = max_over_ranks(e0.elapsed_time(e1) / ku, world)
+        result["unfused"] = {"value": amp_updates_step * world / (msu / 1e3), "ms_per_step": msu,
+                             "launches_per_step": pu_i.stats()["n_launches"] + pu_n.stats()["n_launches"] + 2,
+                             "fidelity": Fu, "speedup_of_value": (amp_updates_step * world / (ms / 1e3))
+                             / (amp_updates_step * world / (msu / 1e3))}
+        del pu_i, pu_n
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        xh = torch.empty(1 << M, dtype=torch.complex64, pin_memory=True)
+        xh.numpy()[:] = x
+        ke = max(1, min(args.steps, 5))
+        import ctypes
+        lib = qs.load_library()
+        Fv, Nv = ctypes.c_double(), ctypes.c_double()
+
+        def e2e_step():
+            qs._check(lib.qsim_set_state(xin.handle, ctypes.c_void_p(xh.data_ptr()), 0))
+            p_ideal.execute(ideal, xin)
+            p_noisy.execute(noisy, xin)
+            qs._check(lib.qsim_fidelity(ideal.handle, noisy.handle, ctypes.byref(Fv), ctypes.byref(Nv)))
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = max_over_ranks((time.perf_counter() - t0) / ke, world)
+        result["e2e"] = {"value": amp_updates_step * world / dt, "unit": "amp-updates/s",
+                         "ms_per_step": dt * 1e3, "h2d_bytes_per_step": int(x.nbytes),
+                         "d2h_bytes_per_step": 24, "steps": ke}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, ng, dt, nt = oracle_sample(M, c["noisy"], x, budget_s=15.0)
+        result["cpu_baseline"] = {"value": v, "unit": "amp-updates/s", "cores": nt, "kind": "oracle",
+                                  "sample": f"first {ng} gates of the noisy circuit at M={M} "
+                                            f"(complex128), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+# ---------------------------------------------------------- reference arm ---
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands, on the host cores, same metric and config;
+    each step is a bounded sample (the first gates of the noisy circuit)."""
+    if rank != 0:
+        return
+    from workloads import generators as W
+    import oracle
+
+    wl = WORKLOADS[args.workload]
+    M = wl["M"]
+    c = W.circuit_c2_qft(M, sigma=wl["sigma"])
+    x = W.random_state(M, seed=2)
+    orc = oracle.Oracle()
+    nt = oracle.default_threads()
+    psi = x.astype(np.complex128)
+    t0 = time.perf_counter()
+    orc.apply_circuit(psi, c["noisy"][:1], nthreads=nt)
+    t1 = time.perf_counter() - t0
+    total_steps = args.steps + args.warmup
+    per_step = max(1, int(min(8.0, 150.0 / max(1, total_steps)) / max(t1, 1e-6)))
+    g = 1
+    for _ in range(args.warmup):
+        orc.apply_circuit(psi, c["noisy"][g:g + per_step], nthreads=nt)
+        g = (g + per_step) % len(c["noisy"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sel = c["noisy"][g:g + per_step]
+        if len(sel) < per_step:
+            g = 0
+            sel = c["noisy"][:per_step]
+        orc.apply_circuit(psi, sel, nthreads=nt)
+        g += per_step
+    dt = (time.perf_counter() - t0) / args.steps
+    v = per_step * float(1 << M) / dt
+    sample = f"{per_step} consecutive gates of the noisy circuit per step at M={M} (complex128)"
+    print(json.dumps({
+        "impl": "reference", "metric": "amplitude-updates/s", "value": v, "unit": "amp-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "complex128",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "M": M, "circuit": "qft", "sigma": wl["sigma"]},
+        "cpu_baseline": {"value": v, "unit": "amp-updates/s", "cores": nt, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "amp-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist_init(world, local)
+    run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * qsim.h -- C ABI of the GB300 error-injecting state-vector simulator.
+ *
+ * What the library computes (Obenland & Despain, "A Parallel Quantum Computer
+ * Simulator"):
+ *   - Section 1.2: an M-qubit register is a vector of 2^M complex amplitudes;
+ *     the index of an amplitude is the bit value of its basis state (qubit q =
+ *     bit q of the index, bit 0 least significant); the probability of a
+ *     state is |amplitude|^2.
+ *   - Section 1.3: a gate is a 2^M x 2^M matrix times that vector.
+ *   - Section 2.1 (Figure 3): a gate on one target bit is a 2x2 operation on
+ *     every pair of states whose indices differ only in that bit; a
+ *     controlled gate (Table 1 / Figure 2, Section 2.0's one-, two- and
+ *     three-bit controlled-NOTs) applies it only where all control bits are 1.
+ *   - Sections 1.4 / 2.0: operational errors are deviations of the rotation
+ *     angles; the library applies gates that already carry their errors, and
+ *     builds erroneous gates itself for error trajectories.
+ *   - Fidelity of the noisy state against the error-free state:
+ *     F = |<ideal|noisy>|^2 (not renormalised) with the noisy norm beside it.
+ *
+ * Conventions for every entry point:
+ *   - Return value: QSIM_OK (0) or a negative QSIM_E* code.  On an error the
+ *     thread-local message of qsim_last_error() says what failed; no output is
+ *     written.  QSIM_ECUDA means a CUDA call failed; after a sticky device
+ *     error every later call fails too.
+ *   - Amplitudes are interleaved complex numbers (re, im): float pairs for
+ *     QSIM_C64, double pairs for QSIM_C128, index order as above.
+ *   - Host arrays passed in (gates, matrices, error angles) are read during
+ *     the call and may be freed when it returns; the caller owns them.
+ *     Output buffers belong to the caller.
+ *   - Work on a state runs on that state's CUDA stream (qsim_set_stream;
+ *     default: the legacy default stream), in call order.  Calls that return
+ *     host values wait for that stream; the others return once the work is
+ *     queued.
+ *   - Nothing here is thread-safe for one state or plan used from several
+ *     host threads at once; distinct states and plans are independent.
+ */
+#ifndef QSIM_H_
+#define QSIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define QSIM_OK 0
+#define QSIM_EINVAL (-1)      /* bad argument: qubit out of range, repeated qubit, bad M, ... */
+#define QSIM_ENOMEM (-2)      /* device allocation failed or over the budget */
+#define QSIM_ECUDA (-3)       /* a CUDA call failed */
+#define QSIM_ETIMEOUT (-4)    /* a bounded device wait ran out */
+#define QSIM_EBUSY (-5)       /* the serving queue is full */
+#define QSIM_EUNSUPPORTED (-6)/* a valid request this build does not handle */
+
+/* Largest qubit count accepted (2^34 complex64 amplitudes = 128 GiB). */
+#define QSIM_MAX_QUBITS 34
+
+typedef enum { QSIM_C64 = 0, QSIM_C128 = 1 } qsim_prec;
+
+/* One gate (Section 2.0): a 2x2 complex matrix U applied to the target qubit
+ * where every control qubit is 1 (Section 2.1).  U is row-major with
+ * interleaved real and imaginary parts: U00re, U00im, U01re, U01im, U10re,
+ * U10im, U11re, U11im.  X, CNOT and Toffoli are U = X with 0, 1 or 2
+ * controls; a rotation gate carries its (erroneous) angle inside U.
+ * 80 bytes, no padding. */
+typedef struct qsim_gate {
+    double U[8];
+    int32_t target;
+    int32_t ncontrols;   /* 0, 1 or 2 */
+    int32_t controls[2]; /* distinct, != target; entries past ncontrols are ignored */
+} qsim_gate;
+
+/* How a circuit is executed.  Every mode computes the same gates in the same
+ * order; they differ in how many gates one pass over the state vector applies. */
+typedef enum {
+    QSIM_MODE_AUTO = 0,     /* the autotuned choice for (M, precision) */
+    QSIM_MODE_UNFUSED = 1,  /* one kernel launch per gate */
+    QSIM_MODE_TILED = 2,    /* shared-memory tiles: many gates per pass over the vector */
+    QSIM_MODE_FUSED = 3     /* runs of gates merged into dense 2^k x 2^k blocks (tensor cores) */
+} qsim_mode;
+
+typedef struct qsim_opts {
+    int32_t mode;       /* qsim_mode */
+    int32_t fuse_k;     /* QSIM_MODE_FUSED block width 2..5; 0 = default */
+    int32_t tile_bits;  /* QSIM_MODE_TILED tile size 2^tile_bits amplitudes, 6..13; 0 = default */
+    int32_t use_graph;  /* 1: a plan replays its launches as one captured CUDA graph */
+} qsim_opts;
+
+/* Counts describing one execution of a plan. */
+typedef struct qsim_plan_stats {
+    int64_t n_gates;       /* gate records in the circuit */
+    int64_t n_passes;      /* passes over the whole state vector */
+    int64_t n_launches;    /* kernel launches per execution */
+    int32_t mode;          /* the mode actually used */
+    int32_t tile_bits;     /* tile size used (QSIM_MODE_TILED) */
+    int32_t fuse_k;        /* block width used (QSIM_MODE_FUSED) */
+    int32_t n_blocks;      /* fused blocks (QSIM_MODE_FUSED) */
+    double algo_bytes;     /* algorithmic device-memory bytes (read + write) per execution */
+    double amp_updates;    /* n_gates * 2^M */
+} qsim_plan_stats;
+
+typedef struct qsim_state qsim_state;   /* opaque; owned by the library */
+typedef struct qsim_plan qsim_plan;     /* opaque; owned by the library */
+
+/* -------------------------------------------------------------- states */
+
+/* Allocate a 2^M-amplitude state on the current CUDA device and set it to
+ * |0...0> (Section 1.2, Figure 1(a)).  M in [1, QSIM_MAX_QUBITS].
+ * QSIM_ENOMEM if the device has no room. */
+int qsim_alloc(int M, qsim_prec prec, qsim_state **out);
+
+/* Use caller-owned device memory (2^M amplitudes, 16-byte aligned) as a
+ * state, without initialising it.  The memory must outlive the state;
+ * qsim_free leaves it alone. */
+int qsim_wrap(void *device_amps, int M, qsim_prec prec, qsim_state **out);
+
+/* Release a state (and its amplitudes if qsim_alloc made them).  NULL is a
+ * no-op.  Waits for the state's stream first. */
+void qsim_free(qsim_state *st);
+
+/* Run the state's work on this cudaStream_t (NULL = legacy default stream). */
+int qsim_set_stream(qsim_state *st, void *cuda_stream);
+
+/* M, precision and device address of the amplitudes. Any output may be NULL. */
+int qsim_state_info(const qsim_state *st, int *M, int *prec, void **device_amps);
+
+/* |0...0> */
+int qsim_reset(qsim_state *st);
+
+/* Copy 2^M amplitudes in from `amps` (host memory, or device memory if
+ * on_device != 0).  Host copies wait for the state's stream. */
+int qsim_set_state(qsim_state *st, const void *amps, int on_device);
+
+/* Copy the 2^M amplitudes out to `amps` (host, or device if on_device != 0).
+ * Host copies wait for the state's stream. */
+int qsim_get_state(const qsim_state *st, void *amps, int on_device);
+
+/* dst := src (same M and precision), on dst's stream after src's queued work. */
+int qsim_copy_state(qsim_state *dst, const qsim_state *src);
+
+/* --------------------------------------------------------------- gates */
+
+/* Apply one gate (Section 2.1, Figure 3): for every index i with bit `target`
+ * 0 and all control bits 1, (a_i, a_j) <- U (a_i, a_j), j = i | 2^target.
+ * U as in qsim_gate.  QSIM_EINVAL for an out-of-range or repeated qubit,
+ * ncontrols outside 0..2, or a non-finite U. */
+int qsim_apply_gate(qsim_state *st, const double U[8], int target,
+                    const int *controls, int ncontrols);
+
+/* Apply n gates in order (Section 2.0: a circuit given as logic gates).
+ * opts may be NULL (QSIM_MODE_AUTO).  Equivalent to qsim_plan_create +
+ * qsim_plan_execute(plan, st, NULL) + qsim_plan_destroy. */
+int qsim_apply_circuit(qsim_state *st, const qsim_gate *gates, size_t n,
+                       const qsim_opts *opts);
+
+/* ---------------------------------------------------------------- plans */
+
+/* Check and compile a circuit for states of M qubits and one precision:
+ * classify gates, group them into passes or fused blocks, build the fused
+ * matrices (FP64 products rounded once to the state precision) and copy the
+ * tables to the device.  The plan may be executed any number of times. */
+int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n,
+                     const qsim_opts *opts, qsim_plan **out);
+
+/* dst := circuit(src).  src == NULL or src == dst runs in place; otherwise
+ * src is left untouched (same M and precision).  Runs on dst's stream after
+ * src's queued work. */
+int qsim_plan_execute(const qsim_plan *plan, qsim_state *dst, const qsim_state *src);
+
+int qsim_plan_stats_get(const qsim_plan *plan, qsim_plan_stats *out);
+
+/* Release a plan; NULL is a no-op.  Waits for the device. */
+void qsim_plan_destroy(qsim_plan *plan);
+
+/* Per-launch timing, for profiling.  While enabled (enable != 0), every
+ * qsim_plan_execute records a CUDA event before its first launch and after
+ * each launch, on dst's stream, without waiting.  Timing is ignored for
+ * executions replayed from a CUDA graph. */
+int qsim_plan_set_timing(qsim_plan *plan, int enable);
+
+/* Wait for the recorded events and report, for each launch index j < n_max
+ * of one execution: ms[j] = milliseconds summed over the timed executions,
+ * bytes[j] = algorithmic bytes of that launch, kind[j] = 0 single gate,
+ * 1 tile pass, 2 fused block.  *executions = number of timed executions.
+ * Any output array may be NULL.  Clears the record. */
+int qsim_plan_timing(qsim_plan *plan, int64_t n_max, double *ms, double *bytes, int32_t *kind,
+                     int64_t *executions);
+
+/* ------------------------------------------------------------ reductions */
+
+/* F = |sum_i conj(ideal_i) noisy_i|^2 and norm_noisy = sum_i |noisy_i|^2,
+ * accumulated in FP64 in a fixed order (deterministic).  Runs on noisy's
+ * stream after ideal's queued work; waits for it.  F or norm_noisy may be
+ * NULL.  Both states must have equal M and precision. */
+int qsim_fidelity(const qsim_state *ideal, const qsim_state *noisy,
+                  double *F, double *norm_noisy);
+
+/* norm = sum_i |a_i|^2 (Section 1.2), FP64 accumulation. */
+int qsim_norm(const qsim_state *st, double *norm);
+
+/* p_i = |a_i|^2 for all 2^M states (Section 1.2, Figure 1) into `out`:
+ * float for QSIM_C64, double for QSIM_C128; host memory, or device memory if
+ * on_device != 0. */
+int qsim_probabilities(const qsim_state *st, void *out, int on_device);
+
+/* --------------------------------------------------------- trajectories */
+
+typedef struct qsim_traj_opts {
+    int32_t fuse_k;     /* fused block width 2..5; 0 = autotuned */
+    int32_t use_graph;  /* 1: the launch is replayed from a captured CUDA graph */
+    int32_t reserved[2];
+} qsim_traj_opts;
+
+/* T error trajectories of one circuit (Sections 1.4, 2.0: every gate's angle
+ * deviates), all started from |0...0>, in one persistent kernel launch.
+ * Gate g of trajectory t is U_g . exp(-i eps[t*n+g]/2 (axis_g . sigma)),
+ * built on the device in FP64; axis_g = (0,0,0) means gate g takes no error.
+ * err_axis: n x 3 doubles; eps: T x n doubles (host).  F_out[t] (host, T
+ * doubles, may be NULL) receives each trajectory's fidelity against the
+ * error-free run; *mean and *var (may be NULL) the mean and unbiased
+ * variance of F.  complex64 amplitudes, M in [1, 20].  Synchronous. */
+int qsim_run_trajectories(int M, const qsim_gate *ideal, const double *err_axis, size_t n,
+                          const double *eps, int T, const qsim_traj_opts *opts,
+                          double *F_out, double *mean, double *var);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *qsim_last_error(void);
+
+/* Library version string. */
+const char *qsim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H_ */

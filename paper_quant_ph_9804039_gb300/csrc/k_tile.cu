@@ -1,0 +1,158 @@
+// Tile-pass kernel: many gates per pass over the state vector.
+//
+// Section 2.1 (Figure 3) applies a gate to every pair of states that differ in
+// the target bit.  Any set S of b qubits splits the 2^M vector into 2^(M-b)
+// independent tiles of 2^b amplitudes (all indices that agree outside S), and
+// every gate whose target lies in S maps each tile onto itself.  A pass loads
+// one tile into shared memory, applies a whole run of such gates to it in
+// circuit order, and writes it back: one read and one write of the vector for
+// the run instead of one per gate.
+//
+// S always holds the L lowest qubits (so a tile is made of contiguous runs of
+// 2^L amplitudes, which keeps device-memory access coalesced) and up to
+// kMaxTileHigh chosen higher qubits.  Controls outside S are constant over a
+// tile (the gate is skipped for tiles where they are not all one); diagonal
+// gates may target a qubit outside S, which makes them one factor per tile
+// (K_SCALE).  The pass may read from one vector and write to another.
+#include "cx.cuh"
+#include "qsim_internal.h"
+
+namespace qs {
+namespace {
+
+template <typename T2>
+__device__ __forceinline__ void tile_apply(T2 *s, int n, const TileOp<T2> &op, uint64_t base) {
+    const uint32_t lmask = op.lmask;
+    if (op.kind == K_SCALE) {
+        const T2 f = (base & op.gsel) ? op.u[3] : op.u[0];
+        for (int u = threadIdx.x; u < n; u += blockDim.x)
+            if ((uint32_t(u) & lmask) == lmask) s[u] = cmul(f, s[u]);
+        return;
+    }
+    const int tl = int(op.tl);
+    if (op.kind == K_DIAG || op.kind == K_PHASE1) {
+        const T2 u00 = op.u[0], u11 = op.u[3];
+        const bool skip0 = op.kind == K_PHASE1;
+        for (int u = threadIdx.x; u < n; u += blockDim.x) {
+            if ((uint32_t(u) & lmask) != lmask) continue;
+            const bool up = (u >> tl) & 1;
+            if (!up && skip0) continue;
+            s[u] = cmul(up ? u11 : u00, s[u]);
+        }
+        return;
+    }
+    const int half = n >> 1;
+    const uint32_t tb = 1u << tl;
+    if (op.kind == K_SWAPX) {
+        for (int p = threadIdx.x; p < half; p += blockDim.x) {
+            const uint32_t i = uint32_t(insert0(uint64_t(p), tl));
+            if ((i & lmask) != lmask) continue;
+            const T2 x = s[i];
+            s[i] = s[i | tb];
+            s[i | tb] = x;
+        }
+        return;
+    }
+    const T2 u00 = op.u[0], u01 = op.u[1], u10 = op.u[2], u11 = op.u[3];
+    for (int p = threadIdx.x; p < half; p += blockDim.x) {
+        const uint32_t i = uint32_t(insert0(uint64_t(p), tl));
+        if ((i & lmask) != lmask) continue;
+        const T2 x = s[i], y = s[i | tb];
+        s[i] = cmad2(u00, x, u01, y);
+        s[i | tb] = cmad2(u10, x, u11, y);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) k_tile_pass(typename CxT<R>::T *dst,
+                                                   const typename CxT<R>::T *src,
+                                                   TilePassDesc d, const TileOp<typename CxT<R>::T> *__restrict__ ops,
+                                                   uint64_t ntiles) {
+    using T2 = typename CxT<R>::T;
+    constexpr int V = CxT<R>::kVec;  // amplitudes per 16-byte access
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *s = reinterpret_cast<T2 *>(smem_raw);
+    __shared__ uint64_t hoff[1 << kMaxTileHigh];
+
+    const int n = 1 << d.b;
+    const uint32_t lowmask = (1u << d.L) - 1;
+    for (int k = threadIdx.x; k < (1 << d.nh); k += blockDim.x) {
+        uint64_t off = 0;
+        for (int j = 0; j < d.nh; ++j)
+            if ((k >> j) & 1) off |= uint64_t(1) << d.hpos[j];
+        hoff[k] = off;
+    }
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint64_t base = 0;
+        for (int j = 0; j < d.nout; ++j)
+            if ((tile >> j) & 1) base |= uint64_t(1) << d.opos[j];
+        __syncthreads();  // hoff ready; the previous tile's stores have read s
+        for (int u = threadIdx.x * V; u < n; u += blockDim.x * V) {
+            const uint64_t g = base | hoff[u >> d.L] | (uint32_t(u) & lowmask);
+            if constexpr (V == 2) {
+                const float4 v = *reinterpret_cast<const float4 *>(src + g);
+                *reinterpret_cast<float4 *>(s + u) = v;
+            } else {
+                s[u] = src[g];
+            }
+        }
+        __syncthreads();
+        for (int k = 0; k < d.op_count; ++k) {
+            const TileOp<T2> op = ops[d.op_begin + k];
+            if ((base & op.gmask) != op.gmask) continue;  // uniform over the block
+            tile_apply(s, n, op, base);
+            __syncthreads();
+        }
+        for (int u = threadIdx.x * V; u < n; u += blockDim.x * V) {
+            const uint64_t g = base | hoff[u >> d.L] | (uint32_t(u) & lowmask);
+            if constexpr (V == 2) {
+                *reinterpret_cast<float4 *>(dst + g) = *reinterpret_cast<const float4 *>(s + u);
+            } else {
+                dst[g] = s[u];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int tile_max_bits(qsim_prec prec) { return prec == QSIM_C64 ? 13 : 12; }
+
+int tile_prepare(qsim_prec prec) {
+    static int configured[64][2];  // per device
+    int dev = 0;
+    QS_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && configured[dev][prec]) return QSIM_OK;
+    if (prec == QSIM_C64)
+        QS_CUDA(cudaFuncSetAttribute(k_tile_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    else
+        QS_CUDA(cudaFuncSetAttribute(k_tile_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    if (dev < 64) configured[dev][prec] = 1;
+    return QSIM_OK;
+}
+
+int launch_tile_pass(void *dst, const void *src, int M, qsim_prec prec, const TilePassDesc &d,
+                     const void *ops_dev, cudaStream_t s) {
+    const uint64_t ntiles = uint64_t(1) << (M - d.b);
+    const size_t smem = (size_t(1) << d.b) * amp_bytes(prec);
+    const int threads = d.b >= 10 ? 512 : (d.b >= 8 ? 128 : 32);
+    if (int rc = tile_prepare(prec)) return rc;
+    int per_sm = int((200 * 1024) / (smem + 2048));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2048 / threads) per_sm = 2048 / threads;
+    uint64_t grid = uint64_t(num_sms()) * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (prec == QSIM_C64) {
+        k_tile_pass<float><<<unsigned(grid), threads, smem, s>>>(
+            static_cast<float2 *>(dst), static_cast<const float2 *>(src), d,
+            static_cast<const TileOp<float2> *>(ops_dev), ntiles);
+    } else {
+        k_tile_pass<double><<<unsigned(grid), threads, smem, s>>>(
+            static_cast<double2 *>(dst), static_cast<const double2 *>(src), d,
+            static_cast<const TileOp<double2> *>(ops_dev), ntiles);
+    }
+    QS_CHECK_LAUNCH("tile pass launch");
+    return QSIM_OK;
+}
+
+}  // namespace qs

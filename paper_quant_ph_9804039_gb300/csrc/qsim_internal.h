@@ -1,0 +1,111 @@
+// Internal declarations shared by the translation units of the CUDA path.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "qsim.h"
+
+namespace qs {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);  // records the message, returns QSIM_ECUDA
+#define QS_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return qs::cuda_fail(e_, #call); \
+    } while (0)
+#define QS_CHECK_LAUNCH(what)                           \
+    do {                                                \
+        cudaError_t e_ = cudaGetLastError();            \
+        if (e_ != cudaSuccess) return qs::cuda_fail(e_, what); \
+    } while (0)
+
+int num_sms();  // streaming multiprocessors of the current device
+
+// ------------------------------------------------------------------- gates
+// Gate kinds, chosen from the matrix on the host:
+//   DENSE  : general 2x2
+//   DIAG   : U01 = U10 = 0
+//   PHASE1 : U01 = U10 = 0 and U00 = 1 exactly (only target-1 states change)
+//   SWAPX  : U = X exactly (a pure exchange, no arithmetic)
+//   SCALE  : (tile passes only) a diagonal gate whose target lies outside the
+//            tile: one factor per tile, U00 or U11 chosen by the tile's index.
+enum Kind : uint32_t { K_DENSE = 0, K_DIAG = 1, K_PHASE1 = 2, K_SWAPX = 3, K_SCALE = 4 };
+
+struct Gate {
+    double U[8];
+    int t;
+    int nc;
+    int c[2];
+    uint64_t cmask;  // all control bits
+    Kind kind;
+    bool nondiag() const { return kind == K_DENSE || kind == K_SWAPX; }
+};
+
+// Validate a record and classify its matrix.  Returns QSIM_OK or QSIM_EINVAL.
+int make_gate(int M, const double *U, int target, const int *controls, int ncontrols, Gate *out);
+
+// Algorithmic bytes (read + write) of one gate applied on its own.
+double gate_bytes(const Gate &g, int M, size_t amp_bytes);
+
+// ------------------------------------------------------------------- state
+struct State {
+    int M;
+    qsim_prec prec;
+    void *amps;
+    bool owned;
+    cudaStream_t stream;
+    double *scratch;     // reduction partials; the last 4 doubles hold the result
+    int scratch_blocks;  // partial slots (3 doubles each)
+    cudaEvent_t ev;      // orders work across states' streams
+};
+
+inline size_t amp_bytes(qsim_prec p) { return p == QSIM_C64 ? 8 : 16; }
+
+// ------------------------------------------------------ single-gate kernels
+int launch_gate(void *amps, int M, qsim_prec prec, const Gate &g, cudaStream_t s);
+
+// -------------------------------------------------------------- tile pass
+// A pass holds a tile of 2^b amplitudes in shared memory: the L lowest qubits
+// plus nh chosen higher qubits (hpos).  The remaining nout qubits (opos)
+// number the tiles.  Every gate of the pass is applied to the tile in order.
+constexpr int kMaxTileHigh = 8;
+struct TilePassDesc {
+    int b, L, nh, nout;
+    int hpos[kMaxTileHigh];
+    int opos[QSIM_MAX_QUBITS];
+    int op_begin, op_count;
+};
+
+template <typename T2>
+struct TileOp {
+    T2 u[4];          // U00, U01, U10, U11 in the state precision
+    uint32_t kind;    // Kind
+    uint32_t tl;      // target position inside the tile (K_SCALE: unused)
+    uint32_t lmask;   // control bits inside the tile (tile-local positions)
+    uint32_t pad;
+    uint64_t gmask;   // control bits outside the tile (global positions)
+    uint64_t gsel;    // K_SCALE: global target bit
+};
+
+int launch_tile_pass(void *dst, const void *src, int M, qsim_prec prec, const TilePassDesc &d,
+                     const void *ops_dev, cudaStream_t s);
+int tile_max_bits(qsim_prec prec);
+int tile_prepare(qsim_prec prec);  // one-time kernel attributes (call before any stream capture)
+
+// -------------------------------------------------------------- reductions
+// Results land in scratch[result_offset .. +3): (norm, re <i|n>, im <i|n>).
+int launch_reduce(const void *ideal, const void *noisy, int M, qsim_prec prec, double *scratch,
+                  int scratch_blocks, cudaStream_t s);
+int launch_probabilities(const void *amps, int M, qsim_prec prec, void *out, cudaStream_t s);
+int launch_zero_state(void *amps, int M, qsim_prec prec, cudaStream_t s);
+constexpr int kReduceSlots = 2048;  // max partial blocks
+
+}  // namespace qs
+
+// The opaque ABI handle is the internal state record.
+struct qsim_state : qs::State {};

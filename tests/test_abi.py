@@ -1,0 +1,79 @@
+"""The C-ABI library loads and exports every function include/qsim.h declares
+(CPU only: no compute call is made)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+import paper_quant_ph_9804039_gb300 as qs
+from workloads.generators import GATE_DTYPE
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(qsim_\w+)\s*\(", text))
+    return names
+
+
+def test_library_builds_and_loads():
+    lib = qs.load_library()
+    assert b"sm_103a" in lib.qsim_version()
+
+
+def test_every_declared_symbol_is_exported():
+    lib = qs.load_library()
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    assert {s[0] for s in qs.SIGNATURES} == declared_functions()
+
+
+def test_gate_record_layout_matches_workloads():
+    assert qs.GATE_DTYPE == GATE_DTYPE and qs.GATE_DTYPE.itemsize == 80
+
+
+def test_last_error_empty_at_start():
+    lib = qs.load_library()
+    assert lib.qsim_last_error() == b""
+
+
+def test_invalid_arguments_rejected_on_host():
+    """Argument checks happen before any CUDA call, so they run without a GPU."""
+    lib = qs.load_library()
+    h = ctypes.c_void_p()
+    assert lib.qsim_alloc(0, 0, ctypes.byref(h)) == qs.QSIM_EINVAL
+    assert lib.qsim_alloc(qs.MAX_QUBITS + 1, 0, ctypes.byref(h)) == qs.QSIM_EINVAL
+    assert lib.qsim_alloc(4, 7, ctypes.byref(h)) == qs.QSIM_EINVAL
+    assert b"precision" in lib.qsim_last_error()
+    g = np.zeros(1, dtype=GATE_DTYPE)
+    g["target"] = 5
+    o = qs.Opts(2, 0, 0, 0)
+    assert lib.qsim_plan_create(4, 0, ctypes.c_void_p(g.ctypes.data), 1, ctypes.byref(o),
+                                ctypes.byref(h)) == qs.QSIM_EINVAL
+    assert b"target" in lib.qsim_last_error()
+    g["target"] = 0
+    g["ncontrols"] = 1
+    g["controls"][0][0] = 0
+    assert lib.qsim_plan_create(4, 0, ctypes.c_void_p(g.ctypes.data), 1, ctypes.byref(o),
+                                ctypes.byref(h)) == qs.QSIM_EINVAL
+    g["ncontrols"] = 0
+    g["U"][0][0] = np.nan
+    assert lib.qsim_plan_create(4, 0, ctypes.c_void_p(g.ctypes.data), 1, ctypes.byref(o),
+                                ctypes.byref(h)) == qs.QSIM_EINVAL
+    o = qs.Opts(2, 0, 14, 0)
+    g["U"][0][0] = 1.0
+    assert lib.qsim_plan_create(4, 0, ctypes.c_void_p(g.ctypes.data), 1, ctypes.byref(o),
+                                ctypes.byref(h)) == qs.QSIM_EINVAL
