@@ -28,7 +28,8 @@ namespace {
 
 template <typename R>
 struct GateK {
-    typename CxT<R>::T u00, u01, u10, u11;
+    typename CxT<R>::T u00, u01, u10, u11;  // hi parts (the entries, for double)
+    typename CxT<R>::T l00, l01, l10, l11;  // lo parts (complex64 only)
     uint64_t lowctl;   // control bits tested per amplitude
     uint64_t setmask;  // bits forced to one after insertion
     int t;
@@ -43,14 +44,13 @@ __device__ __forceinline__ uint64_t expand(uint64_t p, int nins, const int *ins)
     return p;
 }
 
-template <typename T2>
-__device__ __forceinline__ T2 gate_lo_val(uint32_t kind, T2 u00, T2 u01, T2 u10, T2 u11, T2 own,
-                                          T2 partner, bool upper) {
+template <typename T2, typename G>
+__device__ __forceinline__ T2 gate_lo_val(uint32_t kind, const G &g, T2 own, T2 partner, bool upper) {
     // upper: this amplitude has target bit 1
     if (kind == K_SWAPX) return partner;
-    if (kind == K_DIAG) return cmul(upper ? u11 : u00, own);
-    if (kind == K_PHASE1) return upper ? cmul(u11, own) : own;
-    return upper ? cmad2(u10, partner, u11, own) : cmad2(u00, own, u01, partner);
+    if (kind == K_DIAG) return upper ? cmulx(g.u11, g.l11, own) : cmulx(g.u00, g.l00, own);
+    if (kind == K_PHASE1) return upper ? cmulx(g.u11, g.l11, own) : own;
+    return upper ? cmad2x(g.u10, g.l10, partner, g.u11, g.l11, own) : cmad2x(g.u00, g.l00, own, g.u01, g.l01, partner);
 }
 
 // ---------------------------------------------------------------- hi
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(256) k_gate_hi_f(float2 *__restrict__ a, uint6
         if (KIND == K_PHASE1) {  // i enumerates the target-1 states
             float4 v = *pi;
             float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);
-            if (m0) x0 = cmul(g.u11, x0);
-            if (m1) x1 = cmul(g.u11, x1);
+            if (m0) x0 = cmulx(g.u11, g.l11, x0);
+            if (m1) x1 = cmulx(g.u11, g.l11, x1);
             *pi = make_float4(x0.x, x0.y, x1.x, x1.y);
             continue;
         }
@@ -81,11 +81,11 @@ __global__ void __launch_bounds__(256) k_gate_hi_f(float2 *__restrict__ a, uint6
             if (m0) { ra0 = b0; rb0 = a0; }
             if (m1) { ra1 = b1; rb1 = a1; }
         } else if (KIND == K_DIAG) {
-            if (m0) { ra0 = cmul(g.u00, a0); rb0 = cmul(g.u11, b0); }
-            if (m1) { ra1 = cmul(g.u00, a1); rb1 = cmul(g.u11, b1); }
+            if (m0) { ra0 = cmulx(g.u00, g.l00, a0); rb0 = cmulx(g.u11, g.l11, b0); }
+            if (m1) { ra1 = cmulx(g.u00, g.l00, a1); rb1 = cmulx(g.u11, g.l11, b1); }
         } else {
-            if (m0) { ra0 = cmad2(g.u00, a0, g.u01, b0); rb0 = cmad2(g.u10, a0, g.u11, b0); }
-            if (m1) { ra1 = cmad2(g.u00, a1, g.u01, b1); rb1 = cmad2(g.u10, a1, g.u11, b1); }
+            if (m0) { ra0 = cmad2x(g.u00, g.l00, a0, g.u01, g.l01, b0); rb0 = cmad2x(g.u10, g.l10, a0, g.u11, g.l11, b0); }
+            if (m1) { ra1 = cmad2x(g.u00, g.l00, a1, g.u01, g.l01, b1); rb1 = cmad2x(g.u10, g.l10, a1, g.u11, g.l11, b1); }
         }
         *pi = make_float4(ra0.x, ra0.y, ra1.x, ra1.y);
         *pj = make_float4(rb0.x, rb0.y, rb1.x, rb1.y);
@@ -136,11 +136,11 @@ __global__ void __launch_bounds__(256) k_gate_lo_f(float2 *__restrict__ a, uint6
             if (KIND == K_SWAPX) {
                 if (m0) { r0 = x1; r1 = x0; }
             } else if (KIND == K_DIAG) {
-                if (m0) { r0 = cmul(g.u00, x0); r1 = cmul(g.u11, x1); }
+                if (m0) { r0 = cmulx(g.u00, g.l00, x0); r1 = cmulx(g.u11, g.l11, x1); }
             } else if (KIND == K_PHASE1) {
-                if (m0) r1 = cmul(g.u11, x1);
+                if (m0) r1 = cmulx(g.u11, g.l11, x1);
             } else {
-                if (m0) { r0 = cmad2(g.u00, x0, g.u01, x1); r1 = cmad2(g.u10, x0, g.u11, x1); }
+                if (m0) { r0 = cmad2x(g.u00, g.l00, x0, g.u01, g.l01, x1); r1 = cmad2x(g.u10, g.l10, x0, g.u11, g.l11, x1); }
             }
         } else {
             const bool upper = (i >> g.t) & 1;
@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(256) k_gate_lo_f(float2 *__restrict__ a, uint6
                 w1.x = __shfl_xor_sync(0xffffffffu, x1.x, lm);
                 w1.y = __shfl_xor_sync(0xffffffffu, x1.y, lm);
             }
-            if (m0) r0 = gate_lo_val(KIND, g.u00, g.u01, g.u10, g.u11, x0, w0, upper);
-            if (m1) r1 = gate_lo_val(KIND, g.u00, g.u01, g.u10, g.u11, x1, w1, upper);
+            if (m0) r0 = gate_lo_val(KIND, g, x0, w0, upper);
+            if (m1) r1 = gate_lo_val(KIND, g, x1, w1, upper);
         }
         *pi = make_float4(r0.x, r0.y, r1.x, r1.y);
     }
@@ -173,19 +173,20 @@ __global__ void __launch_bounds__(256) k_gate_lo_d(double2 *__restrict__ a, uint
             w.x = __shfl_xor_sync(0xffffffffu, x.x, lm);
             w.y = __shfl_xor_sync(0xffffffffu, x.y, lm);
         }
-        if (m) a[i] = gate_lo_val(KIND, g.u00, g.u01, g.u10, g.u11, x, w, upper);
+        if (m) a[i] = gate_lo_val(KIND, g, x, w, upper);
     }
 }
 
 // ---------------------------------------------------------------- small
-template <typename T2>
-__global__ void k_gate_small(T2 *__restrict__ a, int M, uint32_t kind, T2 u00, T2 u01, T2 u10, T2 u11,
-                             int t, uint64_t cmask) {
+template <typename R>
+__global__ void k_gate_small(typename CxT<R>::T *__restrict__ a, int M, uint32_t kind, GateK<R> g,
+                             uint64_t cmask) {
+    using T2 = typename CxT<R>::T;
     const uint64_t npairs = uint64_t(1) << (M - 1);
-    const uint64_t tb = uint64_t(1) << t;
+    const uint64_t tb = uint64_t(1) << g.t;
     for (uint64_t p = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < npairs;
          p += uint64_t(gridDim.x) * blockDim.x) {
-        const uint64_t i = insert0(p, t);
+        const uint64_t i = insert0(p, g.t);
         if ((i & cmask) != cmask) continue;
         const uint64_t j = i | tb;
         T2 x = a[i], y = a[j];
@@ -193,11 +194,11 @@ __global__ void k_gate_small(T2 *__restrict__ a, int M, uint32_t kind, T2 u00, T
             a[i] = y;
             a[j] = x;
         } else if (kind == K_DIAG || kind == K_PHASE1) {
-            a[i] = cmul(u00, x);
-            a[j] = cmul(u11, y);
+            a[i] = cmulx(g.u00, g.l00, x);
+            a[j] = cmulx(g.u11, g.l11, y);
         } else {
-            a[i] = cmad2(u00, x, u01, y);
-            a[j] = cmad2(u10, x, u11, y);
+            a[i] = cmad2x(g.u00, g.l00, x, g.u01, g.l01, y);
+            a[j] = cmad2x(g.u10, g.l10, x, g.u11, g.l11, y);
         }
     }
 }
@@ -205,10 +206,20 @@ __global__ void k_gate_small(T2 *__restrict__ a, int M, uint32_t kind, T2 u00, T
 template <typename R>
 GateK<R> make_k(const Gate &g) {
     GateK<R> k{};
-    k.u00 = mk(R(g.U[0]), R(g.U[1]));
-    k.u01 = mk(R(g.U[2]), R(g.U[3]));
-    k.u10 = mk(R(g.U[4]), R(g.U[5]));
-    k.u11 = mk(R(g.U[6]), R(g.U[7]));
+    typename CxT<R>::T *hi[4] = {&k.u00, &k.u01, &k.u10, &k.u11};
+    typename CxT<R>::T *lo[4] = {&k.l00, &k.l01, &k.l10, &k.l11};
+    for (int e = 0; e < 4; ++e) {
+        if constexpr (sizeof(R) == 4) {
+            float hr, lr, hi_, li;
+            split_f(g.U[2 * e], hr, lr);
+            split_f(g.U[2 * e + 1], hi_, li);
+            *hi[e] = mk(hr, hi_);
+            *lo[e] = mk(lr, li);
+        } else {
+            *hi[e] = mk(R(g.U[2 * e]), R(g.U[2 * e + 1]));
+            *lo[e] = mk(R(0), R(0));
+        }
+    }
     k.t = g.t;
     return k;
 }
@@ -258,8 +269,7 @@ int launch_gate(void *amps, int M, qsim_prec prec, const Gate &g, cudaStream_t s
         const int lob = 6;
         if (M < 8) {
             GateK<float> k = make_k<float>(g);
-            k_gate_small<float2><<<grid_for(uint64_t(1) << (M - 1), 256), 256, 0, s>>>(
-                a, M, g.kind, k.u00, k.u01, k.u10, k.u11, g.t, g.cmask);
+            k_gate_small<float><<<grid_for(uint64_t(1) << (M - 1), 256), 256, 0, s>>>(a, M, g.kind, k, g.cmask);
         } else if (g.t >= lob) {
             GateK<float> k = make_k<float>(g);
             place_bits(g, lob, true, k);
@@ -277,8 +287,7 @@ int launch_gate(void *amps, int M, qsim_prec prec, const Gate &g, cudaStream_t s
         const int lob = 5;
         if (M < 8) {
             GateK<double> k = make_k<double>(g);
-            k_gate_small<double2><<<grid_for(uint64_t(1) << (M - 1), 256), 256, 0, s>>>(
-                a, M, g.kind, k.u00, k.u01, k.u10, k.u11, g.t, g.cmask);
+            k_gate_small<double><<<grid_for(uint64_t(1) << (M - 1), 256), 256, 0, s>>>(a, M, g.kind, k, g.cmask);
         } else if (g.t >= lob) {
             GateK<double> k = make_k<double>(g);
             place_bits(g, lob, true, k);

@@ -24,20 +24,21 @@ template <typename T2>
 __device__ __forceinline__ void tile_apply(T2 *s, int n, const TileOp<T2> &op, uint64_t base) {
     const uint32_t lmask = op.lmask;
     if (op.kind == K_SCALE) {
-        const T2 f = (base & op.gsel) ? op.u[3] : op.u[0];
+        const bool up = (base & op.gsel) != 0;
+        const T2 f = up ? op.u[3] : op.u[0], fl = up ? op.ul[3] : op.ul[0];
         for (int u = threadIdx.x; u < n; u += blockDim.x)
-            if ((uint32_t(u) & lmask) == lmask) s[u] = cmul(f, s[u]);
+            if ((uint32_t(u) & lmask) == lmask) s[u] = cmulx(f, fl, s[u]);
         return;
     }
     const int tl = int(op.tl);
     if (op.kind == K_DIAG || op.kind == K_PHASE1) {
-        const T2 u00 = op.u[0], u11 = op.u[3];
+        const T2 u00 = op.u[0], u11 = op.u[3], l00 = op.ul[0], l11 = op.ul[3];
         const bool skip0 = op.kind == K_PHASE1;
         for (int u = threadIdx.x; u < n; u += blockDim.x) {
             if ((uint32_t(u) & lmask) != lmask) continue;
             const bool up = (u >> tl) & 1;
             if (!up && skip0) continue;
-            s[u] = cmul(up ? u11 : u00, s[u]);
+            s[u] = up ? cmulx(u11, l11, s[u]) : cmulx(u00, l00, s[u]);
         }
         return;
     }
@@ -54,12 +55,13 @@ __device__ __forceinline__ void tile_apply(T2 *s, int n, const TileOp<T2> &op, u
         return;
     }
     const T2 u00 = op.u[0], u01 = op.u[1], u10 = op.u[2], u11 = op.u[3];
+    const T2 l00 = op.ul[0], l01 = op.ul[1], l10 = op.ul[2], l11 = op.ul[3];
     for (int p = threadIdx.x; p < half; p += blockDim.x) {
         const uint32_t i = uint32_t(insert0(uint64_t(p), tl));
         if ((i & lmask) != lmask) continue;
         const T2 x = s[i], y = s[i | tb];
-        s[i] = cmad2(u00, x, u01, y);
-        s[i | tb] = cmad2(u10, x, u11, y);
+        s[i] = cmad2x(u00, l00, x, u01, l01, y);
+        s[i | tb] = cmad2x(u10, l10, x, u11, l11, y);
     }
 }
 

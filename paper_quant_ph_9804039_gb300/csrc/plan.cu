@@ -63,7 +63,18 @@ template <typename T2>
 TileOp<T2> make_tile_op(const Gate &g, const int *loc, uint64_t S) {
     TileOp<T2> op{};
     using R = decltype(T2{}.x);
-    for (int k = 0; k < 4; ++k) op.u[k] = mk(R(g.U[2 * k]), R(g.U[2 * k + 1]));
+    for (int k = 0; k < 4; ++k) {
+        if constexpr (sizeof(R) == 4) {
+            float hr, lr, hi, li;
+            split_f(g.U[2 * k], hr, lr);
+            split_f(g.U[2 * k + 1], hi, li);
+            op.u[k] = mk(hr, hi);
+            op.ul[k] = mk(lr, li);
+        } else {
+            op.u[k] = mk(R(g.U[2 * k]), R(g.U[2 * k + 1]));
+            op.ul[k] = mk(R(0), R(0));
+        }
+    }
     for (int c = 0; c < g.nc; ++c) {
         if (S & bit(g.c[c]))
             op.lmask |= 1u << loc[g.c[c]];
@@ -79,6 +90,7 @@ TileOp<T2> make_tile_op(const Gate &g, const int *loc, uint64_t S) {
             op.gmask |= bit(g.t);
             op.gsel = 0;
             op.u[0] = op.u[3];
+            op.ul[0] = op.ul[3];
         } else {
             op.gsel = bit(g.t);
         }

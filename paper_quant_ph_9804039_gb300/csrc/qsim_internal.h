@@ -83,7 +83,8 @@ struct TilePassDesc {
 
 template <typename T2>
 struct TileOp {
-    T2 u[4];          // U00, U01, U10, U11 in the state precision
+    T2 u[4];          // U00, U01, U10, U11 in the state precision (hi parts for complex64)
+    T2 ul[4];         // lo parts (complex64; zero for complex128)
     uint32_t kind;    // Kind
     uint32_t tl;      // target position inside the tile (K_SCALE: unused)
     uint32_t lmask;   // control bits inside the tile (tile-local positions)
