@@ -205,6 +205,26 @@ int qsim_norm(const qsim_state *st, double *norm);
  * on_device != 0. */
 int qsim_probabilities(const qsim_state *st, void *out, int on_device);
 
+/* Fidelity and norm for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this entry point exists for code that must not
+ * call cudaMalloc -- work being captured into a CUDA graph, plugins whose host
+ * application owns all GPU memory through its own pool, latency-critical
+ * loops -- and so cannot create the qsim_state that qsim_fidelity needs.
+ *
+ * ideal_amps, noisy_amps: caller-owned device arrays of 2^M amplitudes
+ * (16-byte aligned; ideal_amps may be NULL for the norm alone, F is then 0).
+ * Computes the same F = |sum conj(ideal_i) noisy_i|^2 and norm_noisy =
+ * sum |noisy_i|^2 as qsim_fidelity, on cuda_stream (NULL = legacy default),
+ * and waits for it.  Allocates nothing: its scratch is one fixed 1.5 MiB
+ * device array that every GPU which loads the library holds until the
+ * process exits, so M is limited to [1, 32]; larger M returns QSIM_EINVAL
+ * with a message.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array and it keeps the last call's values; calls whose
+ * work overlaps on the GPU (other streams or host threads) race on it. */
+int qsim_fidelity_noalloc(const void *ideal_amps, const void *noisy_amps, int M, qsim_prec prec,
+                          void *cuda_stream, double *F, double *norm_noisy);
+
 /* --------------------------------------------------------- trajectories */
 
 typedef struct qsim_traj_opts {

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("qsim_fidelity", ctypes.c_int, [_vp, _vp, _dp, _dp]),
     ("qsim_norm", ctypes.c_int, [_vp, _dp]),
     ("qsim_probabilities", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    ("qsim_fidelity_noalloc", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
     ("qsim_run_trajectories", ctypes.c_int, [ctypes.c_int, _vp, _dp, ctypes.c_size_t, _dp, ctypes.c_int,
                                              ctypes.POINTER(TrajOpts), _dp, _dp, _dp]),
     ("qsim_last_error", ctypes.c_char_p, []),
