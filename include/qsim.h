@@ -171,6 +171,11 @@ int qsim_plan_execute(const qsim_plan *plan, qsim_state *dst, const qsim_state *
 
 int qsim_plan_stats_get(const qsim_plan *plan, qsim_plan_stats *out);
 
+/* Wait for the device and report whether any kernel of this plan gave up a
+ * bounded wait since the last call: QSIM_OK, or QSIM_ETIMEOUT (the affected
+ * state is then undefined).  Clears the record. */
+int qsim_plan_status(const qsim_plan *plan);
+
 /* Release a plan; NULL is a no-op.  Waits for the device. */
 void qsim_plan_destroy(qsim_plan *plan);
 

@@ -81,6 +81,7 @@ SIGNATURES = [
                                         ctypes.POINTER(_vp)]),
     ("qsim_plan_execute", ctypes.c_int, [_vp, _vp, _vp]),
     ("qsim_plan_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(PlanStats)]),
+    ("qsim_plan_status", ctypes.c_int, [_vp]),
     ("qsim_plan_destroy", None, [_vp]),
     ("qsim_plan_set_timing", ctypes.c_int, [_vp, ctypes.c_int]),
     ("qsim_plan_timing", ctypes.c_int, [_vp, ctypes.c_int64, _dp, _dp, ctypes.POINTER(ctypes.c_int32),
@@ -268,6 +269,10 @@ class Plan:
     def execute(self, dst: State, src: State | None = None):
         _check(_lib.qsim_plan_execute(self._h, dst._h, src._h if src is not None else None))
         return dst
+
+    def status(self):
+        """Raise if a kernel of this plan gave up a bounded wait (waits for the device)."""
+        _check(_lib.qsim_plan_status(self._h))
 
     def set_timing(self, enable: bool = True):
         _check(_lib.qsim_plan_set_timing(self._h, int(bool(enable))))

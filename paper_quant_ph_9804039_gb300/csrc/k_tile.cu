@@ -13,37 +13,146 @@
 // kMaxTileHigh chosen higher qubits.  Controls outside S are constant over a
 // tile (the gate is skipped for tiles where they are not all one); diagonal
 // gates may target a qubit outside S, which makes them one factor per tile
-// (K_SCALE).  The pass may read from one vector and write to another.
+// (K_SCALE).  Runs of phase gates are applied at once as a phase polynomial
+// (K_PHRUN).  The pass may read from one vector and write to another.
 #include "cx.cuh"
 #include "qsim_internal.h"
 
 namespace qs {
 namespace {
 
+template <typename Turn>
+struct RunSmem {
+    Turn cl[16];       // per-tile linear coefficient of each tile-local bit
+    Turn lin_lo[128];  // linear part over local bits [0, 7)
+    Turn lin_hi[128];  // linear part over local bits [7, b)
+    Turn kt;           // constant of the tile
+};
+
+// e^{2 pi i phi / 2^32}: the top 24 bits go through sincospif (exact argument),
+// the low 8 bits (< 3.7e-7 rad) as a first-order rotation.
+__device__ __forceinline__ float2 expi_turns(uint32_t phi) {
+    const int32_t sp = int32_t(phi);
+    const float x = float(sp >> 8) * (1.0f / 8388608.0f);  // (phi >> 8) / 2^23, in [-1, 1)
+    float sn, cs;
+    sincospif(x, &sn, &cs);
+    const float r = float(phi & 255u) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+    return make_float2(fmaf(-sn, r, cs), fmaf(cs, r, sn));
+}
+// e^{2 pi i phi / 2^64}
+__device__ __forceinline__ double2 expi_turns(uint64_t phi) {
+    const double x = double(int64_t(phi)) * (1.0 / 9223372036854775808.0);
+    double sn, cs;
+    sincospi(x, &sn, &cs);
+    return make_double2(cs, sn);
+}
+
 template <typename T2>
-__device__ __forceinline__ void tile_apply(T2 *s, int n, const TileOp<T2> &op, uint64_t base) {
+__device__ void tile_phase_run(T2 *s, int n, const TilePassDesc &d, uint64_t tile,
+                               const unsigned char *__restrict__ rec, RunSmem<TurnT<T2>> &rs) {
+    using Turn = TurnT<T2>;
+    const PhaseRunHdr h = *reinterpret_cast<const PhaseRunHdr *>(rec);
+    const int M = int(h.M);
+    const Turn *c0p = reinterpret_cast<const Turn *>(rec + sizeof(PhaseRunHdr));
+    const Turn *c = c0p + 1;
+    const Turn *w = c + M;
+    const Turn *Q = reinterpret_cast<const Turn *>(rec + h.q_offset);
+    const int b = d.b;
+    const int t = threadIdx.x;
+    if (t < b) {  // linear coefficient of local bit t, given the tile's outside bits
+        const int q = t < d.L ? t : d.hpos[t - d.L];
+        Turn v = c[q];
+        for (int k = 0; k < d.nout; ++k)
+            if ((tile >> k) & 1) v += w[q * M + d.opos[k]];
+        rs.cl[t] = v;
+    } else if (t == 32) {  // constant of the tile
+        Turn v = *c0p;
+        for (int k = 0; k < d.nout; ++k) {
+            if (!((tile >> k) & 1)) continue;
+            const int r = d.opos[k];
+            v += c[r];
+            for (int k2 = k + 1; k2 < d.nout; ++k2)
+                if ((tile >> k2) & 1) v += w[r * M + d.opos[k2]];
+        }
+        rs.kt = v;
+    }
+    __syncthreads();
+    const int bl = b < 7 ? b : 7;
+    const int bh = b - bl;
+    if (t < (1 << bl)) {
+        Turn v = 0;
+        for (int j = 0; j < bl; ++j)
+            if ((t >> j) & 1) v += rs.cl[j];
+        rs.lin_lo[t] = v;
+    }
+    if (t >= 128 && t - 128 < (1 << bh)) {
+        const int v0 = t - 128;
+        Turn v = 0;
+        for (int j = 0; j < bh; ++j)
+            if ((v0 >> j) & 1) v += rs.cl[bl + j];
+        rs.lin_hi[v0] = v;
+    }
+    __syncthreads();
+    const Turn kt = rs.kt;
+    const uint32_t lomask = (1u << bl) - 1;
+    for (int u = t; u < n; u += blockDim.x) {
+        const Turn phi = kt + rs.lin_lo[u & lomask] + rs.lin_hi[u >> bl] + __ldg(Q + u);
+        s[u] = cmul(expi_turns(phi), s[u]);
+    }
+}
+
+// Insert the bits of `mask` (set to one) into x, lowest first.
+__device__ __forceinline__ uint32_t insert_ones(uint32_t x, uint32_t mask) {
+    while (mask) {
+        const int pos = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint32_t lo = x & ((1u << pos) - 1);
+        x = ((x >> pos) << (pos + 1)) | lo | (1u << pos);
+    }
+    return x;
+}
+
+template <typename T2>
+__device__ __forceinline__ void tile_apply(T2 *s, int n, const TileOp<T2> &op, uint64_t base, uint64_t tile,
+                                           const TilePassDesc &d, const unsigned char *runs,
+                                           RunSmem<TurnT<T2>> &rs) {
     const uint32_t lmask = op.lmask;
+    if (op.kind == K_PHRUN) {
+        tile_phase_run(s, n, d, tile, runs + op.gsel, rs);
+        return;
+    }
     if (op.kind == K_SCALE) {
         const bool up = (base & op.gsel) != 0;
         const T2 f = up ? op.u[3] : op.u[0], fl = up ? op.ul[3] : op.ul[0];
-        for (int u = threadIdx.x; u < n; u += blockDim.x)
-            if ((uint32_t(u) & lmask) == lmask) s[u] = cmulx(f, fl, s[u]);
+        const int cnt = n >> __popc(lmask);
+        for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+            const uint32_t u = insert_ones(uint32_t(p), lmask);
+            s[u] = cmulx(f, fl, s[u]);
+        }
         return;
     }
     const int tl = int(op.tl);
-    if (op.kind == K_DIAG || op.kind == K_PHASE1) {
+    const uint32_t tb = 1u << tl;
+    if (op.kind == K_PHASE1) {  // only states with the target and local controls set change
+        const uint32_t m = lmask | tb;
+        const int cnt = n >> __popc(m);
+        const T2 u11 = op.u[3], l11 = op.ul[3];
+        for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+            const uint32_t u = insert_ones(uint32_t(p), m);
+            s[u] = cmulx(u11, l11, s[u]);
+        }
+        return;
+    }
+    if (op.kind == K_DIAG) {
         const T2 u00 = op.u[0], u11 = op.u[3], l00 = op.ul[0], l11 = op.ul[3];
-        const bool skip0 = op.kind == K_PHASE1;
-        for (int u = threadIdx.x; u < n; u += blockDim.x) {
-            if ((uint32_t(u) & lmask) != lmask) continue;
-            const bool up = (u >> tl) & 1;
-            if (!up && skip0) continue;
-            s[u] = up ? cmulx(u11, l11, s[u]) : cmulx(u00, l00, s[u]);
+        const int cnt = n >> __popc(lmask);
+        for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+            const uint32_t u = insert_ones(uint32_t(p), lmask);
+            s[u] = (u & tb) ? cmulx(u11, l11, s[u]) : cmulx(u00, l00, s[u]);
         }
         return;
     }
     const int half = n >> 1;
-    const uint32_t tb = 1u << tl;
     if (op.kind == K_SWAPX) {
         for (int p = threadIdx.x; p < half; p += blockDim.x) {
             const uint32_t i = uint32_t(insert0(uint64_t(p), tl));
@@ -66,15 +175,15 @@ __device__ __forceinline__ void tile_apply(T2 *s, int n, const TileOp<T2> &op, u
 }
 
 template <typename R>
-__global__ void __launch_bounds__(512) k_tile_pass(typename CxT<R>::T *dst,
-                                                   const typename CxT<R>::T *src,
+__global__ void __launch_bounds__(512) k_tile_pass(typename CxT<R>::T *dst, const typename CxT<R>::T *src,
                                                    TilePassDesc d, const TileOp<typename CxT<R>::T> *__restrict__ ops,
-                                                   uint64_t ntiles) {
+                                                   const unsigned char *__restrict__ runs, uint64_t ntiles) {
     using T2 = typename CxT<R>::T;
     constexpr int V = CxT<R>::kVec;  // amplitudes per 16-byte access
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *s = reinterpret_cast<T2 *>(smem_raw);
     __shared__ uint64_t hoff[1 << kMaxTileHigh];
+    __shared__ RunSmem<TurnT<T2>> rs;
 
     const int n = 1 << d.b;
     const uint32_t lowmask = (1u << d.L) - 1;
@@ -102,7 +211,7 @@ __global__ void __launch_bounds__(512) k_tile_pass(typename CxT<R>::T *dst,
         for (int k = 0; k < d.op_count; ++k) {
             const TileOp<T2> op = ops[d.op_begin + k];
             if ((base & op.gmask) != op.gmask) continue;  // uniform over the block
-            tile_apply(s, n, op, base);
+            tile_apply(s, n, op, base, tile, d, runs, rs);
             __syncthreads();
         }
         for (int u = threadIdx.x * V; u < n; u += blockDim.x * V) {
@@ -134,24 +243,26 @@ int tile_prepare(qsim_prec prec) {
 }
 
 int launch_tile_pass(void *dst, const void *src, int M, qsim_prec prec, const TilePassDesc &d,
-                     const void *ops_dev, cudaStream_t s) {
+                     const void *ops_dev, const void *runs_dev, cudaStream_t s) {
     const uint64_t ntiles = uint64_t(1) << (M - d.b);
     const size_t smem = (size_t(1) << d.b) * amp_bytes(prec);
-    const int threads = d.b >= 10 ? 512 : (d.b >= 8 ? 128 : 32);
+    // >= 256 threads: the phase-run set-up uses threads 0..255
+    const int threads = d.b >= 10 ? 512 : 256;
     if (int rc = tile_prepare(prec)) return rc;
-    int per_sm = int((200 * 1024) / (smem + 2048));
+    int per_sm = int((200 * 1024) / (smem + 4096));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2048 / threads) per_sm = 2048 / threads;
     uint64_t grid = uint64_t(num_sms()) * per_sm;
     if (grid > ntiles) grid = ntiles;
+    const unsigned char *runs = static_cast<const unsigned char *>(runs_dev);
     if (prec == QSIM_C64) {
         k_tile_pass<float><<<unsigned(grid), threads, smem, s>>>(
             static_cast<float2 *>(dst), static_cast<const float2 *>(src), d,
-            static_cast<const TileOp<float2> *>(ops_dev), ntiles);
+            static_cast<const TileOp<float2> *>(ops_dev), runs, ntiles);
     } else {
         k_tile_pass<double><<<unsigned(grid), threads, smem, s>>>(
             static_cast<double2 *>(dst), static_cast<const double2 *>(src), d,
-            static_cast<const TileOp<double2> *>(ops_dev), ntiles);
+            static_cast<const TileOp<double2> *>(ops_dev), runs, ntiles);
     }
     QS_CHECK_LAUNCH("tile pass launch");
     return QSIM_OK;

@@ -23,6 +23,8 @@ struct Step {
     StepType type;
     Gate g;          // S_GATE
     TilePassDesc d;  // S_TILE
+    FusedDesc f;     // S_FUSED
+    size_t rimg;     // S_FUSED: float offset of the block's R image
     double bytes;
 };
 
@@ -40,6 +42,12 @@ struct qsim_plan {
     std::vector<Step> steps;
     void *d_ops = nullptr;
     size_t ops_bytes = 0;
+    void *d_runs = nullptr;  // phase-run records of the tile passes
+    size_t runs_bytes = 0;
+    void *d_rimg = nullptr;  // R_hi / R_lo images of the fused blocks
+    size_t rimg_bytes = 0;
+    int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
+    int fuse_k = 0;
     qsim_plan_stats stats{};
     // CUDA graph of the launches for one (dst, src, stream)
     mutable cudaGraphExec_t gexec = nullptr;
@@ -98,9 +106,102 @@ TileOp<T2> make_tile_op(const Gate &g, const int *loc, uint64_t S) {
     return op;
 }
 
+constexpr int kMinPhaseRun = 6;  // shorter runs of phase gates are applied one by one
+
+// A diagonal gate with unit-modulus entries and at most one control: its
+// phase is a polynomial of degree <= 2 in the index bits.
+bool is_phase_gate(const Gate &g) {
+    if (!(g.kind == K_DIAG || g.kind == K_PHASE1) || g.nc > 1) return false;
+    const double m0 = std::hypot(g.U[0], g.U[1]), m1 = std::hypot(g.U[6], g.U[7]);
+    return std::fabs(m0 - 1.0) <= 1e-12 && std::fabs(m1 - 1.0) <= 1e-12;
+}
+
+// Angle in turns as unsigned fixed point (2^32 or 2^64 = one turn), rounded
+// to nearest.
+template <typename Turn>
+Turn turns(double rad) {
+    double t = rad / (2.0 * M_PI);
+    t -= std::floor(t);  // [0, 1)
+    const double hi = std::floor(t * 4294967296.0);
+    if constexpr (sizeof(Turn) == 4) {
+        return Turn(uint64_t(std::llround(t * 4294967296.0)) & 0xffffffffull);
+    } else {
+        const double lo = (t * 4294967296.0 - hi) * 4294967296.0;  // exact: t has 53 bits
+        return (uint64_t(hi) << 32) + uint64_t(std::llround(lo));
+    }
+}
+
+// Within one pass, move every diagonal gate as late as it can go: just before
+// the first later non-diagonal gate of the pass that acts non-diagonally on
+// one of its qubits (or to the end).  Diagonal gates commute with each other
+// and with any gate that is diagonal on their shared qubits, so the product
+// is unchanged; phase gates gathered this way form long runs.
+std::vector<int> schedule_pass(const std::vector<int> &take, const std::vector<Gate> &gates) {
+    std::vector<int> nd;  // positions (in take) of the non-diagonal gates
+    for (size_t i = 0; i < take.size(); ++i)
+        if (gates[take[i]].nondiag()) nd.push_back(int(i));
+    std::vector<std::vector<int>> slot(nd.size() + 1);
+    for (size_t i = 0; i < take.size(); ++i) {
+        const Gate &g = gates[take[i]];
+        if (g.nondiag()) continue;
+        const uint64_t A = bit(g.t) | g.cmask;
+        size_t k = 0;
+        while (k < nd.size() && (nd[k] < int(i) || !(bit(gates[take[nd[k]]].t) & A))) ++k;
+        slot[k].push_back(take[i]);
+    }
+    std::vector<int> out;
+    out.reserve(take.size());
+    for (size_t k = 0; k <= nd.size(); ++k) {
+        std::stable_partition(slot[k].begin(), slot[k].end(), [&](int gi) { return is_phase_gate(gates[gi]); });
+        out.insert(out.end(), slot[k].begin(), slot[k].end());
+        if (k < nd.size()) out.push_back(take[nd[k]]);
+    }
+    return out;
+}
+
+// Phase polynomial record of a run of phase gates (layout: PhaseRunHdr).
+template <typename Turn>
+size_t add_phase_run(std::vector<unsigned char> &runs, const std::vector<Gate> &gates, const std::vector<int> &run,
+                     int M, const int *pos, int b) {
+    std::vector<Turn> c(size_t(M) + 1, Turn(0)), w(size_t(M) * M, Turn(0));  // c[0] holds c0
+    for (int gi : run) {
+        const Gate &g = gates[gi];
+        const double a = std::atan2(g.U[1], g.U[0]), be = std::atan2(g.U[7], g.U[6]);
+        const Turn ta = turns<Turn>(a), td = turns<Turn>(be - a);
+        if (g.nc == 0) {
+            c[0] += ta;
+            c[1 + g.t] += td;
+        } else {
+            const int q = g.c[0];
+            c[1 + q] += ta;
+            w[size_t(q) * M + g.t] += td;
+            w[size_t(g.t) * M + q] += td;
+        }
+    }
+    const size_t start = (runs.size() + 15) & ~size_t(15);
+    const size_t hdr = sizeof(PhaseRunHdr) + sizeof(Turn) * (size_t(M) + 1 + size_t(M) * M);
+    const size_t qoff = (hdr + 15) & ~size_t(15);
+    runs.resize(start + qoff + sizeof(Turn) * (size_t(1) << b), 0);
+    PhaseRunHdr h{uint32_t(M), uint32_t(b), uint32_t(qoff), 0u};
+    std::memcpy(runs.data() + start, &h, sizeof h);
+    std::memcpy(runs.data() + start + sizeof h, c.data(), sizeof(Turn) * c.size());
+    std::memcpy(runs.data() + start + sizeof h + sizeof(Turn) * c.size(), w.data(), sizeof(Turn) * w.size());
+    Turn *Q = reinterpret_cast<Turn *>(runs.data() + start + qoff);
+    Q[0] = 0;
+    for (uint32_t u = 1; u < (1u << b); ++u) {  // Q[u] = Q[u without its top bit] + that bit's pair terms
+        const int hbit = 31 - __builtin_clz(u);
+        const uint32_t prev = u ^ (1u << hbit);
+        Turn v = Q[prev];
+        for (int j = 0; j < hbit; ++j)
+            if ((prev >> j) & 1) v += w[size_t(pos[j]) * M + pos[hbit]];
+        Q[u] = v;
+    }
+    return start;
+}
+
 // Greedy grouping of the gates into tile passes of at most 2^b amplitudes.
 template <typename T2>
-void plan_tiled(qsim_plan *p, int b_req, std::vector<TileOp<T2>> &ops) {
+void plan_tiled(qsim_plan *p, int b_req, std::vector<TileOp<T2>> &ops, std::vector<unsigned char> &runs) {
     const int M = p->M;
     const int b = std::min(b_req, M);
     const int L = std::min(b, p->prec == QSIM_C64 ? 5 : 4);
@@ -159,9 +260,27 @@ void plan_tiled(qsim_plan *p, int b_req, std::vector<TileOp<T2>> &ops) {
             }
         }
         d.b = d.L + d.nh;
+        int pos[kMaxTileHigh + 8];  // global qubit of each tile-local bit
+        for (int j = 0; j < d.L; ++j) pos[j] = j;
+        for (int j = 0; j < d.nh; ++j) pos[d.L + j] = d.hpos[j];
         d.op_begin = int(ops.size());
-        d.op_count = int(take.size());
-        for (int gi : take) ops.push_back(make_tile_op<T2>(p->gates[gi], loc, S));
+        const std::vector<int> seq = schedule_pass(take, p->gates);
+        for (size_t i = 0; i < seq.size();) {
+            size_t j = i;
+            while (j < seq.size() && is_phase_gate(p->gates[seq[j]])) ++j;
+            if (j - i >= size_t(kMinPhaseRun)) {
+                TileOp<T2> op{};
+                op.kind = K_PHRUN;
+                op.gsel = add_phase_run<TurnT<T2>>(runs, p->gates, std::vector<int>(seq.begin() + i, seq.begin() + j),
+                                                   M, pos, d.b);
+                ops.push_back(op);
+                i = j;
+            } else {
+                if (j == i) j = i + 1;
+                for (; i < j; ++i) ops.push_back(make_tile_op<T2>(p->gates[seq[i]], loc, S));
+            }
+        }
+        d.op_count = int(ops.size()) - d.op_begin;
         st.bytes = 2.0 * std::ldexp(1.0, M) * double(amp_bytes(p->prec));
         p->steps.push_back(st);
         rem.swap(keep);
@@ -178,6 +297,182 @@ int next_event(const qsim_plan *p, cudaStream_t s) {
     return QSIM_OK;
 }
 
+// --------------------------------------------------------------- fused mode
+float tf32_round(float x) {  // round to nearest (ties away), 10 explicit mantissa bits
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        u += 0x1000u;
+        u &= 0xffffe000u;
+    }
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+
+// Product of the block's gates (in order) as a dense 2^k x 2^k matrix, FP64:
+// each gate's 2x2 operation applied to every column (Section 2.1's pair rule
+// on the 2^k-dimensional block space).
+std::vector<double> block_matrix(const std::vector<Gate> &gates, const std::vector<int> &take, const int *bq, int k) {
+    const int n = 1 << k;
+    std::vector<double> U(size_t(2) * n * n, 0.0);  // U[(row * n + col) * 2 + re/im]
+    for (int i = 0; i < n; ++i) U[size_t(2) * (i * n + i)] = 1.0;
+    auto local = [&](int q) {
+        for (int j = 0; j < k; ++j)
+            if (bq[j] == q) return j;
+        return -1;
+    };
+    for (int gi : take) {
+        const Gate &g = gates[gi];
+        const int t = local(g.t);
+        uint32_t cm = 0;
+        for (int c = 0; c < g.nc; ++c) cm |= 1u << local(g.c[c]);
+        for (int i = 0; i < n; ++i) {
+            if ((i >> t) & 1 || (uint32_t(i) & cm) != cm) continue;
+            const int j = i | (1 << t);
+            for (int col = 0; col < n; ++col) {
+                double *a = &U[size_t(2) * (i * n + col)], *b = &U[size_t(2) * (j * n + col)];
+                const double ar = a[0], ai = a[1], br = b[0], bi = b[1];
+                const double *u = g.U;
+                a[0] = u[0] * ar - u[1] * ai + u[2] * br - u[3] * bi;
+                a[1] = u[0] * ai + u[1] * ar + u[2] * bi + u[3] * br;
+                b[0] = u[4] * ar - u[5] * ai + u[6] * br - u[7] * bi;
+                b[1] = u[4] * ai + u[5] * ar + u[6] * bi + u[7] * br;
+            }
+        }
+    }
+    return U;
+}
+
+// R_hi and R_lo of the block in the K-major 128-byte-swizzled layout the MMA
+// reads (rows n = output reals, K = input reals, 32 K per 128-byte chunk).
+void block_rimg(const std::vector<double> &U, int k, float *img) {
+    const int n = 1 << k, KR = 2 * n;
+    const size_t plane = size_t(KR) * KR;
+    for (int r = 0; r < KR; ++r) {
+        for (int kk = 0; kk < KR; ++kk) {
+            const int a = r >> 1, b = kk >> 1;
+            const double ur = U[size_t(2) * (a * n + b)], ui = U[size_t(2) * (a * n + b) + 1];
+            double v;
+            if ((r & 1) == 0) v = (kk & 1) ? -ui : ur;
+            else v = (kk & 1) ? ur : ui;
+            const float hi = tf32_round(float(v));
+            const float lo = tf32_round(float(v - double(hi)));
+            const size_t off = size_t(kk >> 5) * (size_t(KR) * 32) + size_t(r >> 3) * 256 + size_t(r & 7) * 32 +
+                               size_t((((kk & 31) >> 2) ^ (r & 7)) << 2) + size_t(kk & 3);
+            img[off] = hi;
+            img[plane + off] = lo;
+        }
+    }
+}
+
+FusedDesc fused_desc(int M, int k, const int *bq) {
+    FusedDesc d{};
+    d.k = k;
+    uint64_t B = 0;
+    for (int j = 0; j < k; ++j) B |= bit(bq[j]);
+    uint64_t F = 0;
+    int nf = 0;
+    for (int q = 0; q < M && nf < 7; ++q)
+        if (!(B & bit(q))) {
+            F |= bit(q);
+            ++nf;
+        }
+    const uint64_t Uq = B | F;
+    int idx[64];
+    int nu = 0;
+    for (int q = 0; q < M; ++q)
+        if (Uq & bit(q)) idx[q] = nu++;
+    d.runbits = 0;
+    while (d.runbits < M && (Uq & bit(d.runbits))) ++d.runbits;
+    d.nrb = 0;
+    for (int q = d.runbits; q < M; ++q)
+        if (Uq & bit(q)) d.rpos[d.nrb++] = q;
+    d.nout = 0;
+    for (int q = 0; q < M; ++q)
+        if (!(Uq & bit(q))) d.opos[d.nout++] = q;
+    int fq[7], nfq = 0;
+    for (int q = 0; q < M; ++q)
+        if (F & bit(q)) fq[nfq++] = q;
+    for (int a = 0; a < (1 << k); ++a) {
+        uint32_t u = 0;
+        for (int j = 0; j < k; ++j)
+            if ((a >> j) & 1) u |= 1u << idx[bq[j]];
+        d.posA[a] = uint16_t(u);
+    }
+    for (int m = 0; m < 128; ++m) {
+        uint32_t u = 0;
+        for (int j = 0; j < 7; ++j)
+            if ((m >> j) & 1) u |= 1u << idx[fq[j]];
+        d.posM[m] = uint16_t(u);
+    }
+    int rankB[16], rankF[16];  // u bit -> rank in B / F, or -1
+    for (int i = 0; i < 16; ++i) rankB[i] = rankF[i] = -1;
+    for (int j = 0; j < k; ++j) rankB[idx[bq[j]]] = j;
+    for (int j = 0; j < 7; ++j) rankF[idx[fq[j]]] = j;
+    for (int half = 0; half < 2; ++half)
+        for (int v = 0; v < 64; ++v) {
+            int a = 0, m = 0;
+            for (int i = 0; i < 6; ++i) {
+                if (!((v >> i) & 1)) continue;
+                const int ub = 6 * half + i;
+                if (rankB[ub] >= 0) a |= 1 << rankB[ub];
+                if (rankF[ub] >= 0) m |= 1 << rankF[ub];
+            }
+            d.decA[half][v] = uint8_t(a);
+            d.decM[half][v] = uint8_t(m);
+        }
+    return d;
+}
+
+// Greedy grouping into blocks of at most k qubits (every qubit of a gate,
+// controls included, joins the block), padded to exactly k qubits with the
+// lowest free ones.
+void plan_fused(qsim_plan *p, int k, std::vector<float> &rimg) {
+    const int M = p->M;
+    std::vector<int> rem(p->gates.size());
+    for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
+    const size_t per = fused_rimg_floats(k);
+    while (!rem.empty()) {
+        uint64_t defN = 0, defA = 0, Q = 0;
+        std::vector<int> take, keep;
+        for (int gi : rem) {
+            const Gate &g = p->gates[gi];
+            const uint64_t N = g.nondiag() ? bit(g.t) : 0;
+            const uint64_t A = bit(g.t) | g.cmask;
+            const bool blocked = (N & defA) || (A & defN);
+            if (!blocked && __builtin_popcountll(Q | A) <= k) {
+                take.push_back(gi);
+                Q |= A;
+            } else {
+                keep.push_back(gi);
+                defN |= N;
+                defA |= A;
+            }
+        }
+        for (int q = 0; q < M && __builtin_popcountll(Q) < k; ++q) Q |= bit(q);
+        int bq[8], nb = 0;
+        for (int q = 0; q < M; ++q)
+            if (Q & bit(q)) bq[nb++] = q;
+        Step st{};
+        st.type = S_FUSED;
+        st.f = fused_desc(M, k, bq);
+        st.rimg = rimg.size();
+        rimg.resize(rimg.size() + per, 0.f);
+        block_rimg(block_matrix(p->gates, take, bq, k), k, rimg.data() + st.rimg);
+        st.bytes = 2.0 * std::ldexp(1.0, M) * 8.0;
+        p->steps.push_back(st);
+        rem.swap(keep);
+    }
+}
+
+int upload(void **dev, const void *host, size_t bytes, size_t *out_bytes) {
+    *out_bytes = bytes;
+    if (bytes == 0) return QSIM_OK;
+    QS_CUDA(cudaMalloc(dev, bytes));
+    QS_CUDA(cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice));
+    return QSIM_OK;
+}
+
 int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bool timed) {
     const size_t vec_bytes = (size_t(1) << p->M) * amp_bytes(p->prec);
     bool first = true;
@@ -189,7 +484,12 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
         if (timed && !first)
             if (int rc = next_event(p, s)) return rc;
         if (st.type == S_TILE) {
-            if (int rc = launch_tile_pass(dst, first ? src : dst, p->M, p->prec, st.d, p->d_ops, s)) return rc;
+            if (int rc = launch_tile_pass(dst, first ? src : dst, p->M, p->prec, st.d, p->d_ops, p->d_runs, s))
+                return rc;
+        } else if (st.type == S_FUSED) {
+            if (int rc = launch_fused(dst, first ? src : dst, p->M, st.f, static_cast<const float *>(p->d_rimg) + st.rimg,
+                                      p->d_status, s))
+                return rc;
         } else {
             if (first && src != dst) QS_CUDA(cudaMemcpyAsync(dst, src, vec_bytes, cudaMemcpyDeviceToDevice, s));
             if (int rc = launch_gate(dst, p->M, p->prec, st.g, s)) return rc;
@@ -234,16 +534,39 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, co
             return rc;
         }
     }
-    int mode = o.mode == QSIM_MODE_AUTO ? QSIM_MODE_TILED : o.mode;
-    if (mode == QSIM_MODE_FUSED) {
-        set_error("fused mode is not available in this build");
+    if (o.fuse_k != 0 && (o.fuse_k < 2 || o.fuse_k > 5)) {
+        set_error("fuse_k %d outside [2, 5]", o.fuse_k);
         delete p;
-        return QSIM_EUNSUPPORTED;
+        return QSIM_EINVAL;
     }
+    int mode = o.mode == QSIM_MODE_AUTO ? QSIM_MODE_TILED : o.mode;
+    // The tensor-core kernel runs 4- or 5-qubit blocks of complex64 states
+    // with at least 2^(k+7) amplitudes; anything else takes the tile passes.
+    const int k_eff = o.fuse_k == 0 ? 5 : (o.fuse_k <= 4 ? 4 : 5);
+    if (mode == QSIM_MODE_FUSED && (prec != QSIM_C64 || M < k_eff + 7)) mode = QSIM_MODE_TILED;
     p->mode = mode;
+    {
+        cudaError_t e = cudaMalloc(&p->d_status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            int rc = cuda_fail(e, "plan status word");
+            qsim_plan_destroy(p);
+            return rc;
+        }
+    }
     const size_t ab = amp_bytes(prec);
     double bytes = 0;
-    if (mode == QSIM_MODE_UNFUSED) {
+    if (mode == QSIM_MODE_FUSED) {
+        p->fuse_k = k_eff;
+        std::vector<float> rimg;
+        plan_fused(p, k_eff, rimg);
+        int rc = fused_prepare();
+        if (rc == QSIM_OK) rc = upload(&p->d_rimg, rimg.data(), rimg.size() * sizeof(float), &p->rimg_bytes);
+        if (rc) {
+            qsim_plan_destroy(p);
+            return rc;
+        }
+    } else if (mode == QSIM_MODE_UNFUSED) {
         for (const Gate &g : p->gates) {
             Step st{};
             st.type = S_GATE;
@@ -255,27 +578,19 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, co
         const int b = o.tile_bits ? o.tile_bits : default_tile_bits(prec);
         p->tile_bits = std::min(b, M);
         int rc = tile_prepare(prec);
+        std::vector<unsigned char> runs;
         if (rc == QSIM_OK) {
             if (prec == QSIM_C64) {
                 std::vector<TileOp<float2>> ops;
-                plan_tiled(p, b, ops);
-                p->ops_bytes = ops.size() * sizeof(ops[0]);
-                if (!ops.empty()) {
-                    cudaError_t e = cudaMalloc(&p->d_ops, p->ops_bytes);
-                    if (e == cudaSuccess) e = cudaMemcpy(p->d_ops, ops.data(), p->ops_bytes, cudaMemcpyHostToDevice);
-                    if (e != cudaSuccess) rc = cuda_fail(e, "plan table upload");
-                }
+                plan_tiled(p, b, ops, runs);
+                rc = upload(&p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
             } else {
                 std::vector<TileOp<double2>> ops;
-                plan_tiled(p, b, ops);
-                p->ops_bytes = ops.size() * sizeof(ops[0]);
-                if (!ops.empty()) {
-                    cudaError_t e = cudaMalloc(&p->d_ops, p->ops_bytes);
-                    if (e == cudaSuccess) e = cudaMemcpy(p->d_ops, ops.data(), p->ops_bytes, cudaMemcpyHostToDevice);
-                    if (e != cudaSuccess) rc = cuda_fail(e, "plan table upload");
-                }
+                plan_tiled(p, b, ops, runs);
+                rc = upload(&p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
             }
         }
+        if (rc == QSIM_OK) rc = upload(&p->d_runs, runs.data(), runs.size(), &p->runs_bytes);
         if (rc) {
             qsim_plan_destroy(p);
             return rc;
@@ -288,8 +603,8 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, co
     s.n_launches = int64_t(p->steps.size());
     s.mode = mode;
     s.tile_bits = mode == QSIM_MODE_TILED ? p->tile_bits : 0;
-    s.fuse_k = 0;
-    s.n_blocks = 0;
+    s.fuse_k = mode == QSIM_MODE_FUSED ? p->fuse_k : 0;
+    s.n_blocks = mode == QSIM_MODE_FUSED ? int32_t(p->steps.size()) : 0;
     s.algo_bytes = bytes;
     s.amp_updates = double(n) * std::ldexp(1.0, M);
     *out = p;
@@ -380,7 +695,23 @@ void qsim_plan_destroy(qsim_plan *p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     if (p->d_ops) cudaFree(p->d_ops);
+    if (p->d_runs) cudaFree(p->d_runs);
+    if (p->d_rimg) cudaFree(p->d_rimg);
+    if (p->d_status) cudaFree(p->d_status);
     delete p;
+}
+
+int qsim_plan_status(const qsim_plan *p) {
+    if (!p) { set_error("plan is NULL"); return QSIM_EINVAL; }
+    int v = 0;
+    QS_CUDA(cudaDeviceSynchronize());
+    QS_CUDA(cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        QS_CUDA(cudaMemset(p->d_status, 0, sizeof(int)));
+        set_error("a kernel of this plan gave up a bounded wait (status %d)", v);
+        return v;
+    }
+    return QSIM_OK;
 }
 
 int qsim_apply_circuit(qsim_state *st, const qsim_gate *gates, size_t n, const qsim_opts *opts) {
@@ -392,6 +723,7 @@ int qsim_apply_circuit(qsim_state *st, const qsim_gate *gates, size_t n, const q
         cudaError_t e = cudaStreamSynchronize(st->stream);  // the plan's tables must outlive the launches
         if (e != cudaSuccess) rc = cuda_fail(e, "circuit execution");
     }
+    if (rc == QSIM_OK) rc = qsim_plan_status(p);
     qsim_plan_destroy(p);
     return rc;
 }

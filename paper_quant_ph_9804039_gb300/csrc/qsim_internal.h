@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "qsim.h"
@@ -34,7 +35,10 @@ int num_sms();  // streaming multiprocessors of the current device
 //   SWAPX  : U = X exactly (a pure exchange, no arithmetic)
 //   SCALE  : (tile passes only) a diagonal gate whose target lies outside the
 //            tile: one factor per tile, U00 or U11 chosen by the tile's index.
-enum Kind : uint32_t { K_DENSE = 0, K_DIAG = 1, K_PHASE1 = 2, K_SWAPX = 3, K_SCALE = 4 };
+//   PHRUN  : (tile passes only) a run of diagonal gates with unit-modulus
+//            entries and at most one control, applied at once as a phase
+//            polynomial of the index bits (see PhaseRun).
+enum Kind : uint32_t { K_DENSE = 0, K_DIAG = 1, K_PHASE1 = 2, K_SWAPX = 3, K_SCALE = 4, K_PHRUN = 5 };
 
 struct Gate {
     double U[8];
@@ -93,10 +97,46 @@ struct TileOp {
     uint64_t gsel;    // K_SCALE: global target bit
 };
 
+// A run of diagonal gates diag(e^{i a}, e^{i b}) with at most one control
+// multiplies amplitude g by e^{i Phi(g)}, Phi a quadratic polynomial of the
+// index bits: Phi = c0 + sum_q c[q] g_q + sum_{q<r} w[q][r] g_q g_r.  Phases
+// are kept in turns as unsigned fixed point (2^32 per turn for complex64,
+// 2^64 for complex128), so sums wrap exactly modulo 2 pi.  Device record,
+// 16-byte aligned, at TileOp::gsel bytes into the plan's run buffer:
+//   PhaseRunHdr; Turn c0; Turn c[M]; Turn w[M*M] (symmetric, zero diagonal);
+//   then, at q_offset, Turn Q[2^b] = the quadratic part over the pass's tile
+//   qubits, indexed by the tile-local index.
+struct PhaseRunHdr {
+    uint32_t M, b, q_offset, pad;  // q_offset: byte offset of Q from the record start
+};
+template <typename T2>
+using TurnT = typename std::conditional<sizeof(T2) == 8, uint32_t, uint64_t>::type;
+
 int launch_tile_pass(void *dst, const void *src, int M, qsim_prec prec, const TilePassDesc &d,
-                     const void *ops_dev, cudaStream_t s);
+                     const void *ops_dev, const void *runs_dev, cudaStream_t s);
 int tile_max_bits(qsim_prec prec);
 int tile_prepare(qsim_prec prec);  // one-time kernel attributes (call before any stream capture)
+
+// ------------------------------------------------------------ fused blocks
+// Geometry of one fused k-qubit block over a state of M qubits (see
+// k_fused_tc.cu): tile qubits U = B u F (B the block, F the 7 lowest other
+// qubits), tile-local index u = bits of U in ascending order.
+struct FusedDesc {
+    int k;
+    int runbits;                 // qubits 0..runbits-1 are all in U: runs of 2^runbits amplitudes
+    int nrb;                     // qubits of U above the run: k + 7 - runbits
+    int rpos[12];                // their global positions, ascending
+    int nout;                    // qubits outside U (number the tiles)
+    int opos[QSIM_MAX_QUBITS];
+    uint16_t posA[32];           // u of block combination a (sub-vector 0)
+    uint16_t posM[128];          // u of sub-vector m (combination 0)
+    uint8_t decA[2][64];         // a from u: decA[0][u & 63] | decA[1][u >> 6]
+    uint8_t decM[2][64];         // m from u, likewise
+};
+int fused_prepare();
+size_t fused_rimg_floats(int k);  // floats of one block's R_hi + R_lo image
+int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const float *rimg_dev, int *status,
+                 cudaStream_t s);
 
 // -------------------------------------------------------------- reductions
 // Results land in scratch[result_offset .. +3): (norm, re <i|n>, im <i|n>).

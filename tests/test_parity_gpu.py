@@ -140,6 +140,32 @@ def test_qft_complex64(orc, M, mode):
     assert abs(F - Fo) <= TOL64_F and abs(nrm - nrmo) <= TOL64_F
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("M,tile_bits", [(9, 0), (13, 7), (16, 0), (19, 12)])
+def test_phase_runs(orc, prec, M, tile_bits):
+    """Long runs of diagonal gates (Rz-like diag(e^ia, e^ib), controlled
+    phases, on qubits inside and outside the tile) between a few Hadamards:
+    the tiled mode applies each run at once as a phase polynomial."""
+    rng = np.random.default_rng(40 + M)
+    recs = []
+    for layer in range(5):
+        for q in rng.choice(M, size=3, replace=False):
+            recs.append(W.gate_record(W.mat_h(), int(q)))
+        for _ in range(30):
+            t = int(rng.integers(M))
+            if rng.random() < 0.5:
+                U = np.diag(np.exp(1j * rng.uniform(-7, 7, 2)))
+                ctl = ()
+            else:
+                U = W.mat_phase(float(rng.uniform(-7, 7)))
+                ctl = (int(rng.choice([q for q in range(M) if q != t])),)
+            recs.append(W.gate_record(U, t, ctl))
+    recs = W._pack(recs)
+    x, x128 = _input(M, prec)
+    st = qs.State(M, prec).set(x).apply_circuit(recs, mode="tiled", tile_bits=tile_bits)
+    _close(st.get(), orc.run(M, recs, x128, nthreads=NT), prec)
+
+
 @pytest.mark.parametrize("M", [14, 18])
 def test_brickwork_toffoli_complex64(orc, M):
     """The brickwork + Toffoli workload at reduced M, tiled and unfused."""
@@ -251,3 +277,86 @@ def test_full_size_qft_m28():
     Fa, na = qs.fidelity(ideal, a)
     Fb, nb = qs.fidelity(ideal, b)
     assert abs(Fa - Fb) <= TOL64_F and 0.99 < Fa <= 1.0 + TOL64_F
+
+
+# ---------------------------------------------------------------- fused mode
+def _fused_case(orc, M, recs, k, x=None):
+    if x is None:
+        x, x128 = _input(M, "c64")
+    else:
+        x128 = x.astype(np.complex128)
+    plan = qs.Plan(M, recs, mode="fused", fuse_k=k)
+    st = qs.State(M).set(x)
+    plan.execute(st)
+    plan.status()
+    assert plan.stats()["mode"] == qs.MODE_FUSED and plan.stats()["n_blocks"] >= 1
+    _close(st.get(), orc.run(M, recs, x128, nthreads=NT), "c64")
+    return plan
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("M", [12, 13, 16, 20])
+def test_fused_random_circuits(orc, k, M):
+    """Dense k-qubit blocks on the tensor cores (split TF32, FP32 accumulation)."""
+    if M < k + 7:
+        pytest.skip("state smaller than one fused tile")
+    rng = np.random.default_rng(300 + 7 * M + k)
+    _fused_case(orc, M, _rand_gates(rng, M, 120), k)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("qubits", [(0, 1, 2, 3, 4), (12, 13, 14, 15, 16), (0, 3, 7, 11, 16), (1, 2, 9, 10, 15)])
+def test_fused_block_positions(orc, k, qubits):
+    """One block on low, high and mixed qubit positions (tile layouts differ)."""
+    M = 17
+    rng = np.random.default_rng(sum(qubits) + k)
+    qs_ = list(qubits[:k])
+    recs = []
+    for _ in range(40):
+        t = int(rng.choice(qs_))
+        others = [q for q in qs_ if q != t]
+        nc = int(rng.integers(0, 3))
+        ctl = [int(v) for v in rng.choice(others, size=nc, replace=False)] if nc else []
+        recs.append(W.gate_record(W.mat_haar_su2(rng) * np.exp(1j * rng.uniform(0, 6.3)), t, ctl))
+    plan = _fused_case(orc, M, W._pack(recs), k)
+    assert plan.stats()["n_blocks"] == 1
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_fused_qft_and_brickwork(orc, k):
+    M = 18
+    c = W.circuit_c2_qft(M, sigma=1e-4)
+    x, x128 = _input(M, "c64")
+    ideal = qs.State(M).set(x)
+    noisy = qs.State(M).set(x)
+    qs.Plan(M, c["ideal"], mode="fused", fuse_k=k).execute(ideal)
+    pn = qs.Plan(M, c["noisy"], mode="fused", fuse_k=k)
+    pn.execute(noisy)
+    pn.status()
+    ri = orc.run(M, c["ideal"], x128, nthreads=NT)
+    rn = orc.run(M, c["noisy"], x128, nthreads=NT)
+    _close(ideal.get(), ri, "c64")
+    _close(noisy.get(), rn, "c64")
+    F, nrm = qs.fidelity(ideal, noisy)
+    Fo, nrmo = orc.fidelity(ri, rn)
+    assert abs(F - Fo) <= TOL64_F and abs(nrm - nrmo) <= TOL64_F
+    b = W.circuit_c4_brickwork_toffoli(M, layers=8)
+    _fused_case(orc, M, b["noisy"], k, x)
+
+
+def test_fused_out_of_place(orc):
+    import torch
+    M = 16
+    rng = np.random.default_rng(77)
+    recs = _rand_gates(rng, M, 60)
+    x, x128 = _input(M, "c64")
+    s = torch.cuda.Stream()
+    src = qs.State(M, stream=s).set(x)
+    dst = qs.State(M, stream=s)
+    plan = qs.Plan(M, recs, mode="fused")
+    plan.execute(dst, src)
+    s.synchronize()
+    plan.status()
+    _close(dst.get(), orc.run(M, recs, x128, nthreads=NT), "c64")
+    assert np.array_equal(src.get(), x)
+
