@@ -36,6 +36,8 @@ import numpy as np  # noqa: E402
 
 WORKLOADS = {
     "qft-m28-c64": dict(M=28, sigma=1e-4),
+    # smaller case of the same circuit for ncu captures (512 MiB per state, > L2)
+    "qft-m26-c64": dict(M=26, sigma=1e-4),
 }
 
 
@@ -251,7 +253,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": args.workload, "M": M, "circuit": "qft", "sigma": wl["sigma"],
                    "gates_per_circuit": n_logical, "gate_records_per_circuit": int(len(c["noisy"])),
                    "circuits_per_step": 2, "mode": mode, "tile_bits": st_n["tile_bits"],
-                   "passes_per_circuit": st_n["n_passes"], "l2": "inputs larger than L2 (2 GiB per state)",
+                   "passes_per_circuit": st_n["n_passes"], "l2": f"inputs larger than L2 ({(8 << M) >> 20} MiB per state)",
                    "parallelism": f"replicas{world}"},
         "roofline": roofline,
         "gpu_launches": int(launches_step * args.steps),

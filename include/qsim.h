@@ -233,13 +233,34 @@ int qsim_fidelity_noalloc(const void *ideal_amps, const void *noisy_amps, int M,
 /* --------------------------------------------------------- trajectories */
 
 typedef struct qsim_traj_opts {
-    int32_t fuse_k;     /* fused block width 2..5; 0 = autotuned */
-    int32_t use_graph;  /* 1: the launch is replayed from a captured CUDA graph */
+    int32_t fuse_k;     /* reserved for fused blocks: 0 or 1 (one gate at a time) */
+    int32_t use_graph;  /* 1: each run replays a captured CUDA graph */
     int32_t reserved[2];
 } qsim_traj_opts;
 
+typedef struct qsim_traj_plan qsim_traj_plan;  /* opaque; owned by the library */
+
+/* Compile a circuit for up to max_T error trajectories (complex64, M in
+ * [1, 20]): computes the error-free state, allocates the per-CTA workspaces
+ * and picks the tile size by timing the candidates on a short batch (cached
+ * per circuit in the process).  The plan owns its own CUDA stream. */
+int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis, size_t n, int max_T,
+                          const qsim_traj_opts *opts, qsim_traj_plan **out);
+
+/* Run T <= max_T trajectories with errors eps (T x n doubles, host) in one
+ * persistent kernel launch (replayed from a CUDA graph when use_graph is set);
+ * outputs as for qsim_run_trajectories.  Synchronous. */
+int qsim_traj_plan_run(qsim_traj_plan *plan, const double *eps, int T, double *F_out, double *mean,
+                       double *var);
+
+/* Tile size chosen, tile passes per trajectory and the persistent grid size. */
+int qsim_traj_plan_info(const qsim_traj_plan *plan, int *tile_bits, int *n_passes, int *grid);
+
+void qsim_traj_plan_destroy(qsim_traj_plan *plan);
+
 /* T error trajectories of one circuit (Sections 1.4, 2.0: every gate's angle
- * deviates), all started from |0...0>, in one persistent kernel launch.
+ * deviates), all started from |0...0>, in one persistent kernel launch
+ * (qsim_traj_plan_create + qsim_traj_plan_run + qsim_traj_plan_destroy).
  * Gate g of trajectory t is U_g . exp(-i eps[t*n+g]/2 (axis_g . sigma)),
  * built on the device in FP64; axis_g = (0,0,0) means gate g takes no error.
  * err_axis: n x 3 doubles; eps: T x n doubles (host).  F_out[t] (host, T
@@ -249,6 +270,60 @@ typedef struct qsim_traj_opts {
 int qsim_run_trajectories(int M, const qsim_gate *ideal, const double *err_axis, size_t n,
                           const double *eps, int T, const qsim_traj_opts *opts,
                           double *F_out, double *mean, double *var);
+
+/* -------------------------------------------------------------- serving */
+
+/* A request loop with continuous batching.  A request is one simulation as
+ * the paper runs it (Section 2.0): M qubits from |0...0>, the error-free
+ * gates and the erroneous gates applied to two complex64 copies, then F and
+ * the noisy norm (qsim_fidelity).  A scheduler thread admits the oldest
+ * waiting request as soon as a slot is free and its two state vectors fit in
+ * hbm_budget; each slot runs on its own CUDA stream, so admitted requests
+ * overlap on the device.  Results do not depend on the mix. */
+typedef struct qsim_server qsim_server;  /* opaque; owned by the library */
+
+typedef struct qsim_server_opts {
+    uint64_t hbm_budget;  /* bytes of state vectors held at once (2 x 2^M x 8 per request) */
+    int32_t max_slots;    /* requests in flight at once, 1..256 */
+    int32_t mode;         /* qsim_mode of the requests' circuits */
+} qsim_server_opts;
+
+typedef struct qsim_request_result {
+    uint64_t id;
+    int32_t status;      /* QSIM_OK; QSIM_ENOMEM if the request can never fit the budget */
+    int32_t M;
+    int32_t n_gates;
+    int32_t pad;
+    double F, norm;      /* |<ideal|noisy>|^2 and the noisy norm */
+    double t_submit, t_start, t_done;  /* seconds on the server's clock */
+} qsim_request_result;
+
+typedef struct qsim_server_stats {
+    uint64_t n_submitted, n_completed, n_pending;
+    uint64_t bytes_in_use, peak_bytes;  /* state-vector bytes held now / at most */
+    int32_t max_active;                 /* most requests in flight at once */
+    int32_t pad;
+    double now;                         /* the server's clock, seconds */
+} qsim_server_stats;
+
+/* Start a server on the current device (its own memory pool and streams). */
+int qsim_server_create(const qsim_server_opts *opts, qsim_server **out);
+
+/* Queue a request: n gates of the error-free circuit and n of the erroneous
+ * one (copied; checked now, QSIM_EINVAL on a bad gate).  QSIM_EBUSY if 2^20
+ * requests are already waiting.  *id identifies its result. */
+int qsim_server_submit(qsim_server *srv, int M, const qsim_gate *ideal, const qsim_gate *noisy, size_t n,
+                       uint64_t *id);
+
+/* Move up to max finished results into out (completion order), waiting up to
+ * wait_ms for the first one; *nout = how many. */
+int qsim_server_poll(qsim_server *srv, qsim_request_result *out, int max, int *nout, int wait_ms);
+
+int qsim_server_get_stats(qsim_server *srv, qsim_server_stats *out);
+
+/* Finish every queued request, then stop and release everything.  Results
+ * not polled are dropped. */
+void qsim_server_destroy(qsim_server *srv);
 
 /* ---------------------------------------------------------------- misc */
 

@@ -60,6 +60,29 @@ class TrajOpts(ctypes.Structure):
     _fields_ = [("fuse_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_slots", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("n_gates", ctypes.c_int32), ("pad", ctypes.c_int32), ("F", ctypes.c_double),
+                ("norm", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("n_submitted", ctypes.c_uint64), ("n_completed", ctypes.c_uint64), ("n_pending", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64), ("max_active", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("now", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -92,6 +115,17 @@ SIGNATURES = [
     ("qsim_fidelity_noalloc", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
     ("qsim_run_trajectories", ctypes.c_int, [ctypes.c_int, _vp, _dp, ctypes.c_size_t, _dp, ctypes.c_int,
                                              ctypes.POINTER(TrajOpts), _dp, _dp, _dp]),
+    ("qsim_traj_plan_create", ctypes.c_int, [ctypes.c_int, _vp, _dp, ctypes.c_size_t, ctypes.c_int,
+                                             ctypes.POINTER(TrajOpts), ctypes.POINTER(_vp)]),
+    ("qsim_traj_plan_run", ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp, _dp]),
+    ("qsim_traj_plan_info", ctypes.c_int, [_vp, _ip, _ip, _ip]),
+    ("qsim_traj_plan_destroy", None, [_vp]),
+    ("qsim_server_create", ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)]),
+    ("qsim_server_submit", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    ("qsim_server_poll", ctypes.c_int, [_vp, ctypes.POINTER(RequestResult), ctypes.c_int, _ip, ctypes.c_int]),
+    ("qsim_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
+    ("qsim_server_destroy", None, [_vp]),
     ("qsim_last_error", ctypes.c_char_p, []),
     ("qsim_version", ctypes.c_char_p, []),
 ]
@@ -298,6 +332,83 @@ class Plan:
         if h is not None and _lib is not None:
             _lib.qsim_plan_destroy(h)
             self._h = None
+
+
+class TrajPlan:
+    """A circuit compiled for batches of error trajectories (qsim_traj_plan_create)."""
+
+    def __init__(self, M: int, gates, err_axis, max_T: int, use_graph: bool = True):
+        lib = load_library()
+        g = _records(gates)
+        ax = np.ascontiguousarray(err_axis, dtype=np.float64)
+        assert ax.shape == (len(g), 3)
+        self.M, self.n, self.max_T = int(M), len(g), int(max_T)
+        o = TrajOpts(0, int(bool(use_graph)))
+        h = _vp()
+        _check(lib.qsim_traj_plan_create(self.M, _vp(g.ctypes.data), ax.ctypes.data_as(_dp), len(g), self.max_T,
+                                         ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, eps):
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        T = e.shape[0]
+        assert e.shape[1] == self.n
+        F = np.zeros(T)
+        mean, var = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.qsim_traj_plan_run(self._h, e.ctypes.data_as(_dp), T, F.ctypes.data_as(_dp), ctypes.byref(mean),
+                                       ctypes.byref(var)))
+        return F, mean.value, var.value
+
+    def info(self) -> dict:
+        tb, npass, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.qsim_traj_plan_info(self._h, ctypes.byref(tb), ctypes.byref(npass), ctypes.byref(grid)))
+        return {"tile_bits": tb.value, "n_passes": npass.value, "grid": grid.value}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.qsim_traj_plan_destroy(h)
+            self._h = None
+
+
+class Server:
+    """Continuous-batching request loop (qsim_server_*)."""
+
+    def __init__(self, hbm_budget: int, max_slots: int = 8, mode="tiled"):
+        lib = load_library()
+        m = _MODES[mode] if isinstance(mode, str) else int(mode)
+        o = ServerOpts(int(hbm_budget), int(max_slots), m)
+        h = _vp()
+        _check(lib.qsim_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, M: int, ideal, noisy) -> int:
+        gi, gn = _records(ideal), _records(noisy)
+        assert len(gi) == len(gn)
+        rid = ctypes.c_uint64()
+        _check(_lib.qsim_server_submit(self._h, int(M), _vp(gi.ctypes.data), _vp(gn.ctypes.data), len(gi),
+                                       ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, max_results: int = 256, wait_ms: int = 0):
+        buf = (RequestResult * max_results)()
+        n = ctypes.c_int()
+        _check(_lib.qsim_server_poll(self._h, buf, max_results, ctypes.byref(n), int(wait_ms)))
+        return [buf[i].as_dict() for i in range(n.value)]
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(_lib.qsim_server_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.qsim_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def run_trajectories(M: int, gates, err_axis, eps, fuse_k: int = 0, use_graph: bool = False):

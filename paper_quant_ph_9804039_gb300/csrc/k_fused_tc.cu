@@ -14,7 +14,14 @@
 // Precision: complex64 amplitudes, FP32 accumulation.  TF32 keeps 11
 // significant bits, so both operands are split, v = hi + lo with hi and lo
 // rounded to TF32 (to nearest), and D = X_lo R_hi + X_hi R_lo + X_hi R_hi
-// (the lo*lo term is below 2^-22 relative).
+// (the lo*lo term is below 2^-22 relative).  The tensor core's FP32
+// accumulation truncates, which shrinks every output by a fraction of an ulp
+// on average; over many blocks that bias would show in the norm and the
+// fidelity.  A unitary block preserves the norm of every sub-vector, so for
+// blocks the planner has checked to be unitary the epilogue rescales each
+// output sub-vector to its input norm (sums in FP32, rounded to nearest; the
+// correction applied as v + v c with c = (|x|^2 - |y|^2) / (2 |y|^2)), which
+// removes the bias and leaves unbiased rounding.
 //
 // Tile: the k block qubits plus F = the 7 lowest other qubits, 2^(k+7)
 // amplitudes, numbered by a tile-local index u whose bits are the qubits of
@@ -192,6 +199,7 @@ struct SmemCtl {
     uint16_t posM[kMT];
     uint8_t decA[2][64];  // a = decA[0][u & 63] | decA[1][u >> 6]
     uint8_t decM[2][64];  // m = decM[0][u & 63] | decM[1][u >> 6]
+    float2 red[2][kMT];   // per row and column half: (|x|^2, |y|^2)
 };
 
 template <int KF>
@@ -321,17 +329,37 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int half = warp >> 2;
             const uint32_t taddr = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(half * (C::KR / 2));
             const uint32_t pm = ctl.posM[m];
-            if constexpr (C::KR / 2 == 32) {
-                float v[32];
-                tmem_ld32(taddr, v);
+            constexpr int NJ = C::KR / 4;  // amplitudes per thread
+            float sx = 0.f;
+            if (d.unitary) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) buf[ctl.posA[half * 16 + j] | pm] = make_float2(v[2 * j], v[2 * j + 1]);
-            } else {
-                float v[16];
-                tmem_ld16(taddr, v);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) buf[ctl.posA[half * 8 + j] | pm] = make_float2(v[2 * j], v[2 * j + 1]);
+                for (int j = 0; j < NJ; ++j) {
+                    const float2 x = buf[ctl.posA[half * NJ + j] | pm];
+                    sx = fmaf(x.x, x.x, fmaf(x.y, x.y, sx));
+                }
             }
+            float v[2 * NJ];
+            if constexpr (NJ == 16)
+                tmem_ld32(taddr, v);
+            else
+                tmem_ld16(taddr, v);
+            if (d.unitary) {
+                float sy = 0.f;
+#pragma unroll
+                for (int j = 0; j < 2 * NJ; ++j) sy = fmaf(v[j], v[j], sy);
+                ctl.red[half][m] = make_float2(sx, sy);
+                __syncthreads();
+                const float tx = ctl.red[0][m].x + ctl.red[1][m].x;
+                const float ty = ctl.red[0][m].y + ctl.red[1][m].y;
+                // sqrt(tx/ty) - 1 to first order, kept as a small number: the
+                // bias is a fraction of an ulp, so a scale factor near 1 would
+                // round to exactly 1; v + v c rounds to nearest, unbiased.
+                const float c = (tx > 0.f && ty > 0.f) ? (tx - ty) / (2.f * ty) : 0.f;
+#pragma unroll
+                for (int j = 0; j < 2 * NJ; ++j) v[j] = fmaf(v[j], c, v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) buf[ctl.posA[half * NJ + j] | pm] = make_float2(v[2 * j], v[2 * j + 1]);
         }
         tc_fence_before();
         fence_proxy_async();

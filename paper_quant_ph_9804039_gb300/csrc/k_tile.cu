@@ -17,6 +17,7 @@
 // (K_PHRUN).  The pass may read from one vector and write to another.
 #include "cx.cuh"
 #include "qsim_internal.h"
+#include "tile_ops.cuh"
 
 namespace qs {
 namespace {
@@ -101,77 +102,15 @@ __device__ void tile_phase_run(T2 *s, int n, const TilePassDesc &d, uint64_t til
     }
 }
 
-// Insert the bits of `mask` (set to one) into x, lowest first.
-__device__ __forceinline__ uint32_t insert_ones(uint32_t x, uint32_t mask) {
-    while (mask) {
-        const int pos = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const uint32_t lo = x & ((1u << pos) - 1);
-        x = ((x >> pos) << (pos + 1)) | lo | (1u << pos);
-    }
-    return x;
-}
-
 template <typename T2>
 __device__ __forceinline__ void tile_apply(T2 *s, int n, const TileOp<T2> &op, uint64_t base, uint64_t tile,
                                            const TilePassDesc &d, const unsigned char *runs,
                                            RunSmem<TurnT<T2>> &rs) {
-    const uint32_t lmask = op.lmask;
     if (op.kind == K_PHRUN) {
         tile_phase_run(s, n, d, tile, runs + op.gsel, rs);
         return;
     }
-    if (op.kind == K_SCALE) {
-        const bool up = (base & op.gsel) != 0;
-        const T2 f = up ? op.u[3] : op.u[0], fl = up ? op.ul[3] : op.ul[0];
-        const int cnt = n >> __popc(lmask);
-        for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-            const uint32_t u = insert_ones(uint32_t(p), lmask);
-            s[u] = cmulx(f, fl, s[u]);
-        }
-        return;
-    }
-    const int tl = int(op.tl);
-    const uint32_t tb = 1u << tl;
-    if (op.kind == K_PHASE1) {  // only states with the target and local controls set change
-        const uint32_t m = lmask | tb;
-        const int cnt = n >> __popc(m);
-        const T2 u11 = op.u[3], l11 = op.ul[3];
-        for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-            const uint32_t u = insert_ones(uint32_t(p), m);
-            s[u] = cmulx(u11, l11, s[u]);
-        }
-        return;
-    }
-    if (op.kind == K_DIAG) {
-        const T2 u00 = op.u[0], u11 = op.u[3], l00 = op.ul[0], l11 = op.ul[3];
-        const int cnt = n >> __popc(lmask);
-        for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-            const uint32_t u = insert_ones(uint32_t(p), lmask);
-            s[u] = (u & tb) ? cmulx(u11, l11, s[u]) : cmulx(u00, l00, s[u]);
-        }
-        return;
-    }
-    const int half = n >> 1;
-    if (op.kind == K_SWAPX) {
-        for (int p = threadIdx.x; p < half; p += blockDim.x) {
-            const uint32_t i = uint32_t(insert0(uint64_t(p), tl));
-            if ((i & lmask) != lmask) continue;
-            const T2 x = s[i];
-            s[i] = s[i | tb];
-            s[i | tb] = x;
-        }
-        return;
-    }
-    const T2 u00 = op.u[0], u01 = op.u[1], u10 = op.u[2], u11 = op.u[3];
-    const T2 l00 = op.ul[0], l01 = op.ul[1], l10 = op.ul[2], l11 = op.ul[3];
-    for (int p = threadIdx.x; p < half; p += blockDim.x) {
-        const uint32_t i = uint32_t(insert0(uint64_t(p), tl));
-        if ((i & lmask) != lmask) continue;
-        const T2 x = s[i], y = s[i | tb];
-        s[i] = cmad2x(u00, l00, x, u01, l01, y);
-        s[i | tb] = cmad2x(u10, l10, x, u11, l11, y);
-    }
+    tile_gate(s, n, op.kind, op.tl, op.lmask, (base & op.gsel) != 0, op.u, op.ul);
 }
 
 template <typename R>

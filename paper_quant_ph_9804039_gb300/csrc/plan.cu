@@ -48,6 +48,10 @@ struct qsim_plan {
     size_t rimg_bytes = 0;
     int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
     int fuse_k = 0;
+    // non-null: device tables are allocated and freed stream-ordered on this
+    // stream (the serving loop), so creating and releasing a plan never
+    // synchronises the device
+    cudaStream_t alloc_stream = nullptr;
     qsim_plan_stats stats{};
     // CUDA graph of the launches for one (dst, src, stream)
     mutable cudaGraphExec_t gexec = nullptr;
@@ -343,6 +347,23 @@ std::vector<double> block_matrix(const std::vector<Gate> &gates, const std::vect
     return U;
 }
 
+// U^dagger U = I to 1e-10 (FP64).
+bool is_unitary(const std::vector<double> &U, int k) {
+    const int n = 1 << k;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double re = 0, im = 0;
+            for (int r = 0; r < n; ++r) {  // sum_r conj(U[r][i]) U[r][j]
+                const double ar = U[size_t(2) * (r * n + i)], ai = U[size_t(2) * (r * n + i) + 1];
+                const double br = U[size_t(2) * (r * n + j)], bi = U[size_t(2) * (r * n + j) + 1];
+                re += ar * br + ai * bi;
+                im += ar * bi - ai * br;
+            }
+            if (std::fabs(re - (i == j ? 1.0 : 0.0)) > 1e-10 || std::fabs(im) > 1e-10) return false;
+        }
+    return true;
+}
+
 // R_hi and R_lo of the block in the K-major 128-byte-swizzled layout the MMA
 // reads (rows n = output reals, K = input reals, 32 K per 128-byte chunk).
 void block_rimg(const std::vector<double> &U, int k, float *img) {
@@ -458,18 +479,36 @@ void plan_fused(qsim_plan *p, int k, std::vector<float> &rimg) {
         st.f = fused_desc(M, k, bq);
         st.rimg = rimg.size();
         rimg.resize(rimg.size() + per, 0.f);
-        block_rimg(block_matrix(p->gates, take, bq, k), k, rimg.data() + st.rimg);
+        const std::vector<double> U = block_matrix(p->gates, take, bq, k);
+        st.f.unitary = is_unitary(U, k) ? 1 : 0;
+        block_rimg(U, k, rimg.data() + st.rimg);
         st.bytes = 2.0 * std::ldexp(1.0, M) * 8.0;
         p->steps.push_back(st);
         rem.swap(keep);
     }
 }
 
-int upload(void **dev, const void *host, size_t bytes, size_t *out_bytes) {
+int dev_alloc(const qsim_plan *p, void **dev, size_t bytes) {
+    if (p->alloc_stream) QS_CUDA(cudaMallocAsync(dev, bytes, p->alloc_stream));
+    else QS_CUDA(cudaMalloc(dev, bytes));
+    return QSIM_OK;
+}
+
+void dev_free(const qsim_plan *p, void *dev) {
+    if (!dev) return;
+    if (p->alloc_stream) cudaFreeAsync(dev, p->alloc_stream);
+    else cudaFree(dev);
+}
+
+int upload(const qsim_plan *p, void **dev, const void *host, size_t bytes, size_t *out_bytes) {
     *out_bytes = bytes;
     if (bytes == 0) return QSIM_OK;
-    QS_CUDA(cudaMalloc(dev, bytes));
-    QS_CUDA(cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice));
+    if (int rc = dev_alloc(p, dev, bytes)) return rc;
+    // pageable source: the copy has left `host` when the call returns
+    if (p->alloc_stream)
+        QS_CUDA(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, p->alloc_stream));
+    else
+        QS_CUDA(cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice));
     return QSIM_OK;
 }
 
@@ -504,10 +543,10 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
 
 }  // namespace
 
-extern "C" {
+namespace qs {
 
-int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, const qsim_opts *opts,
-                     qsim_plan **out) {
+int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, const qsim_opts *opts,
+                   cudaStream_t alloc_stream, qsim_plan **out) {
     if (!out) { set_error("out is NULL"); return QSIM_EINVAL; }
     if (M < 1 || M > QSIM_MAX_QUBITS) { set_error("M = %d outside [1, %d]", M, QSIM_MAX_QUBITS); return QSIM_EINVAL; }
     if (prec != QSIM_C64 && prec != QSIM_C128) { set_error("unknown precision %d", int(prec)); return QSIM_EINVAL; }
@@ -523,6 +562,7 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, co
     p->M = M;
     p->prec = prec;
     p->opts = o;
+    p->alloc_stream = alloc_stream;
     p->gates.resize(n);
     for (size_t i = 0; i < n; ++i) {
         int rc = make_gate(M, gates[i].U, gates[i].target, gates[i].controls, gates[i].ncontrols, &p->gates[i]);
@@ -546,11 +586,14 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, co
     if (mode == QSIM_MODE_FUSED && (prec != QSIM_C64 || M < k_eff + 7)) mode = QSIM_MODE_TILED;
     p->mode = mode;
     {
-        cudaError_t e = cudaMalloc(&p->d_status, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
-        if (e != cudaSuccess) {
-            int rc = cuda_fail(e, "plan status word");
-            qsim_plan_destroy(p);
+        int rc = dev_alloc(p, reinterpret_cast<void **>(&p->d_status), sizeof(int));
+        if (rc == QSIM_OK) {
+            cudaError_t e = alloc_stream ? cudaMemsetAsync(p->d_status, 0, sizeof(int), alloc_stream)
+                                         : cudaMemset(p->d_status, 0, sizeof(int));
+            if (e != cudaSuccess) rc = cuda_fail(e, "plan status word");
+        }
+        if (rc) {
+            plan_release(p);
             return rc;
         }
     }
@@ -561,9 +604,9 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, co
         std::vector<float> rimg;
         plan_fused(p, k_eff, rimg);
         int rc = fused_prepare();
-        if (rc == QSIM_OK) rc = upload(&p->d_rimg, rimg.data(), rimg.size() * sizeof(float), &p->rimg_bytes);
+        if (rc == QSIM_OK) rc = upload(p, &p->d_rimg, rimg.data(), rimg.size() * sizeof(float), &p->rimg_bytes);
         if (rc) {
-            qsim_plan_destroy(p);
+            plan_release(p);
             return rc;
         }
     } else if (mode == QSIM_MODE_UNFUSED) {
@@ -583,16 +626,16 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, co
             if (prec == QSIM_C64) {
                 std::vector<TileOp<float2>> ops;
                 plan_tiled(p, b, ops, runs);
-                rc = upload(&p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
+                rc = upload(p, &p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
             } else {
                 std::vector<TileOp<double2>> ops;
                 plan_tiled(p, b, ops, runs);
-                rc = upload(&p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
+                rc = upload(p, &p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
             }
         }
-        if (rc == QSIM_OK) rc = upload(&p->d_runs, runs.data(), runs.size(), &p->runs_bytes);
+        if (rc == QSIM_OK) rc = upload(p, &p->d_runs, runs.data(), runs.size(), &p->runs_bytes);
         if (rc) {
-            qsim_plan_destroy(p);
+            plan_release(p);
             return rc;
         }
     }
@@ -609,6 +652,26 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, co
     s.amp_updates = double(n) * std::ldexp(1.0, M);
     *out = p;
     return QSIM_OK;
+}
+
+void plan_release(qsim_plan *p) {
+    if (!p) return;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    dev_free(p, p->d_ops);
+    dev_free(p, p->d_runs);
+    dev_free(p, p->d_rimg);
+    dev_free(p, p->d_status);
+    delete p;
+}
+
+}  // namespace qs
+
+extern "C" {
+
+int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, const qsim_opts *opts,
+                     qsim_plan **out) {
+    return plan_create_on(M, prec, gates, n, opts, nullptr, out);
 }
 
 int qsim_plan_execute(const qsim_plan *p, qsim_state *dst, const qsim_state *src) {
@@ -692,13 +755,7 @@ int qsim_plan_stats_get(const qsim_plan *p, qsim_plan_stats *out) {
 void qsim_plan_destroy(qsim_plan *p) {
     if (!p) return;
     cudaDeviceSynchronize();
-    if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
-    if (p->d_ops) cudaFree(p->d_ops);
-    if (p->d_runs) cudaFree(p->d_runs);
-    if (p->d_rimg) cudaFree(p->d_rimg);
-    if (p->d_status) cudaFree(p->d_status);
-    delete p;
+    plan_release(p);
 }
 
 int qsim_plan_status(const qsim_plan *p) {

@@ -123,6 +123,7 @@ int tile_prepare(qsim_prec prec);  // one-time kernel attributes (call before an
 // qubits), tile-local index u = bits of U in ascending order.
 struct FusedDesc {
     int k;
+    int unitary;                 // the block is unitary: rescale each sub-vector to its input norm
     int runbits;                 // qubits 0..runbits-1 are all in U: runs of 2^runbits amplitudes
     int nrb;                     // qubits of U above the run: k + 7 - runbits
     int rpos[12];                // their global positions, ascending
@@ -150,3 +151,13 @@ constexpr int kReduceSlots = 2048;  // max partial blocks
 
 // The opaque ABI handle is the internal state record.
 struct qsim_state : qs::State {};
+
+namespace qs {
+// Plan creation whose device tables are allocated stream-ordered on
+// alloc_stream (nullptr: plain cudaMalloc), and release without a device
+// synchronisation: the caller guarantees that the plan's work has completed
+// or is ordered before alloc_stream's later work.
+int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, const qsim_opts *opts,
+                   cudaStream_t alloc_stream, qsim_plan **out);
+void plan_release(qsim_plan *p);
+}  // namespace qs

@@ -1,13 +1,549 @@
-// Error trajectories (filled in by the batched kernel).
+// Error trajectories: T runs of one circuit, each with its own operational
+// errors (Sections 1.4 and 2.0: every laser operation's rotation angle
+// deviates), started from |0...0>, each reduced to its fidelity against the
+// error-free run.
+//
+// One persistent kernel launch does all T trajectories.  Each CTA takes the
+// next trajectory from an atomic counter and runs the whole circuit on a
+// private workspace vector (2^M complex64, resident in L2 for the sizes this
+// is meant for) in tile passes, like the single-state tile pass: the gates of
+// a pass are applied to one 2^b tile at a time in shared memory.  At the
+// start of every pass the CTA builds that pass's erroneous gate matrices in
+// FP64, U_g . exp(-i eps[t][g]/2 (n_g . sigma)), and keeps them (hi + lo
+// float parts) in shared memory.  The first pass synthesises |0...0> instead
+// of reading memory; the last pass does not write the vector back but
+// accumulates sum conj(ideal_i) noisy_i against the error-free state, giving
+// F[t] = |<ideal|noisy_t>|^2.
+//
+// A plan (qsim_traj_plan) keeps the pass tables, the error-free state, the
+// workspaces and a captured CUDA graph of [copy errors in, reset counter,
+// kernel, copy fidelities out]; each run replays the graph.  The tile size is
+// chosen by timing the candidates on a short batch (the autotuner), cached
+// per (M, gates) in the process.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "cx.cuh"
 #include "qsim_internal.h"
+#include "tile_ops.cuh"
+
+namespace qs {
+namespace {
+
+struct TrajOp {
+    double U[8];     // error-free matrix
+    double ax[3];    // error axis; (0,0,0): the gate takes no error
+    int gate;        // column of eps
+    uint32_t kind;   // kind of the erroneous gate (a K_* value)
+    uint32_t tl;     // target inside the tile
+    uint32_t lmask;  // controls inside the tile
+    uint32_t pad;
+    uint64_t gmask;  // controls outside the tile
+    uint64_t gsel;   // K_SCALE: the target bit (outside the tile)
+};
+
+constexpr int kMaxPassOps = 256;  // gates per pass (matrices kept in shared memory)
+constexpr int kTrajThreads = 512;
+
+// U . exp(-i e/2 n.sigma) in FP64, split into float hi + lo.
+__device__ void noisy_matrix(const TrajOp &op, double e, float2 *u, float2 *ul) {
+    double r[8];
+    const double nx = op.ax[0], ny = op.ax[1], nz = op.ax[2];
+    if (nx == 0.0 && ny == 0.0 && nz == 0.0) {
+        for (int k = 0; k < 8; ++k) r[k] = op.U[k];
+    } else {
+        double sn, cs;
+        sincos(0.5 * e, &sn, &cs);
+        // E = c I - i s n.sigma = [[c - i s nz, -s ny - i s nx], [s ny - i s nx, c + i s nz]]
+        const double E[8] = {cs, -sn * nz, -sn * ny, -sn * nx, sn * ny, -sn * nx, cs, sn * nz};
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                double re = 0, im = 0;
+                for (int k = 0; k < 2; ++k) {
+                    const double ar = op.U[2 * (2 * i + k)], ai = op.U[2 * (2 * i + k) + 1];
+                    const double br = E[2 * (2 * k + j)], bi = E[2 * (2 * k + j) + 1];
+                    re += ar * br - ai * bi;
+                    im += ar * bi + ai * br;
+                }
+                r[2 * (2 * i + j)] = re;
+                r[2 * (2 * i + j) + 1] = im;
+            }
+    }
+    for (int k = 0; k < 4; ++k) {
+        float hr, lr, hi, li;
+        split_f(r[2 * k], hr, lr);
+        split_f(r[2 * k + 1], hi, li);
+        u[k] = make_float2(hr, hi);
+        ul[k] = make_float2(lr, li);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kTrajThreads) k_trajectories(int M, int npass, const TilePassDesc *__restrict__ passes,
+                                                               const TrajOp *__restrict__ ops,
+                                                               const double *__restrict__ eps, int n, int T,
+                                                               const float2 *__restrict__ ideal, float2 *work,
+                                                               double *__restrict__ F_out, unsigned *counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float2 mu[kMaxPassOps][4], ml[kMaxPassOps][4];
+    __shared__ uint64_t hoff[1 << kMaxTileHigh];
+    __shared__ double red[2][kTrajThreads / 32];
+    __shared__ int s_t;
+    float2 *s = reinterpret_cast<float2 *>(smem_raw);
+    float2 *ws = work + (size_t(blockIdx.x) << M);
+    const int tid = threadIdx.x;
+
+    for (;;) {
+        if (tid == 0) s_t = int(atomicAdd(counter, 1u));
+        __syncthreads();
+        const int t = s_t;
+        if (t >= T) break;
+        double ore = 0.0, oim = 0.0;
+        for (int p = 0; p < npass; ++p) {
+            const TilePassDesc &d = passes[p];
+            const int nops = d.op_count;
+            for (int j = tid; j < nops; j += blockDim.x) {
+                const TrajOp &op = ops[d.op_begin + j];
+                noisy_matrix(op, eps[size_t(t) * n + op.gate], mu[j], ml[j]);
+            }
+            for (int k = tid; k < (1 << d.nh); k += blockDim.x) {
+                uint64_t off = 0;
+                for (int j = 0; j < d.nh; ++j)
+                    if ((k >> j) & 1) off |= uint64_t(1) << d.hpos[j];
+                hoff[k] = off;
+            }
+            __syncthreads();
+            const int nt = 1 << d.b;
+            const uint32_t lowmask = (1u << d.L) - 1;
+            const uint64_t ntiles = uint64_t(1) << d.nout;
+            for (uint64_t tile = 0; tile < ntiles; ++tile) {
+                uint64_t base = 0;
+                for (int j = 0; j < d.nout; ++j)
+                    if ((tile >> j) & 1) base |= uint64_t(1) << d.opos[j];
+                for (int u = tid * 2; u < nt; u += blockDim.x * 2) {
+                    const uint64_t g = base | hoff[u >> d.L] | (uint32_t(u) & lowmask);
+                    float4 v;
+                    if (p == 0)
+                        v = make_float4(g == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+                    else
+                        v = *reinterpret_cast<const float4 *>(ws + g);
+                    *reinterpret_cast<float4 *>(s + u) = v;
+                }
+                __syncthreads();
+                for (int j = 0; j < nops; ++j) {
+                    const TrajOp &op = ops[d.op_begin + j];
+                    if ((base & op.gmask) != op.gmask) continue;
+                    tile_gate(s, nt, op.kind, op.tl, op.lmask, (base & op.gsel) != 0, mu[j], ml[j]);
+                    __syncthreads();
+                }
+                if (p + 1 < npass) {
+                    for (int u = tid * 2; u < nt; u += blockDim.x * 2) {
+                        const uint64_t g = base | hoff[u >> d.L] | (uint32_t(u) & lowmask);
+                        *reinterpret_cast<float4 *>(ws + g) = *reinterpret_cast<const float4 *>(s + u);
+                    }
+                } else {  // last pass: overlap with the error-free state
+                    for (int u = tid * 2; u < nt; u += blockDim.x * 2) {
+                        const uint64_t g = base | hoff[u >> d.L] | (uint32_t(u) & lowmask);
+                        const float4 a = *reinterpret_cast<const float4 *>(ideal + g);
+                        const float4 b = *reinterpret_cast<const float4 *>(s + u);
+                        ore += double(fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w))));
+                        oim += double(fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, -a.w * b.z))));
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        ore = warp_sum(ore);
+        oim = warp_sum(oim);
+        if ((tid & 31) == 0) {
+            red[0][tid >> 5] = ore;
+            red[1][tid >> 5] = oim;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0, b = 0;
+            for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+                a += red[0][w];
+                b += red[1][w];
+            }
+            F_out[t] = a * a + b * b;
+        }
+        __syncthreads();
+    }
+}
+
+bool is_zero_axis(const double *a) { return a[0] == 0.0 && a[1] == 0.0 && a[2] == 0.0; }
+
+// Structure of a gate once its error is applied.
+Kind erroneous_kind(const Gate &g, const double *ax) {
+    if (is_zero_axis(ax)) return g.kind;
+    if ((g.kind == K_DIAG || g.kind == K_PHASE1) && ax[0] == 0.0 && ax[1] == 0.0) return K_DIAG;
+    return K_DENSE;
+}
+
+}  // namespace
+}  // namespace qs
 
 using namespace qs;
 
-extern "C" int qsim_run_trajectories(int M, const qsim_gate *ideal, const double *err_axis, size_t n,
-                                     const double *eps, int T, const qsim_traj_opts *opts, double *F_out,
-                                     double *mean, double *var) {
-    (void)M; (void)ideal; (void)err_axis; (void)n; (void)eps; (void)T; (void)opts;
-    (void)F_out; (void)mean; (void)var;
-    set_error("error trajectories are not available in this build");
-    return QSIM_EUNSUPPORTED;
+struct qsim_traj_plan {
+    int M = 0;
+    int n = 0;
+    int tile_bits = 0;
+    int grid = 0;
+    int max_T = 0;
+    std::vector<TilePassDesc> passes;
+    std::vector<TrajOp> ops;
+    TilePassDesc *d_passes = nullptr;
+    TrajOp *d_ops = nullptr;
+    float2 *d_ideal = nullptr;
+    float2 *d_work = nullptr;
+    double *d_eps = nullptr;
+    double *d_F = nullptr;
+    unsigned *d_counter = nullptr;
+    double *h_eps = nullptr;  // pinned staging
+    double *h_F = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_T = -1;
+    int use_graph = 0;
+    size_t smem = 0;
+};
+
+namespace {
+
+// Tile passes over the error-free circuit's structure (the same greedy
+// grouping as the single-state passes; no phase runs, since every
+// trajectory's phases differ).
+int build_passes(qsim_traj_plan *p, const std::vector<Gate> &gates, const double *ax, int b_req) {
+    const int M = p->M;
+    const int b = std::min(b_req, M);
+    const int L = std::min(b, 5);
+    const int cap = std::min(b - L, kMaxTileHigh);
+    auto bitq = [](int q) { return uint64_t(1) << q; };
+    std::vector<Kind> kind(gates.size());
+    for (size_t i = 0; i < gates.size(); ++i) kind[i] = erroneous_kind(gates[i], ax + 3 * i);
+    auto nondiag = [&](size_t i) { return kind[i] == K_DENSE || kind[i] == K_SWAPX; };
+    std::vector<int> rem(gates.size());
+    for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
+    p->passes.clear();
+    p->ops.clear();
+    bool first = true;  // an empty circuit still gets one (empty) pass
+    while (first || !rem.empty()) {
+        first = false;
+        uint64_t defN = 0, defA = 0, high = 0;
+        int nh = 0;
+        std::vector<int> take, keep;
+        for (int gi : rem) {
+            const Gate &g = gates[gi];
+            const uint64_t N = nondiag(gi) ? bitq(g.t) : 0;
+            const uint64_t A = bitq(g.t) | g.cmask;
+            bool ok = !((N & defA) || (A & defN)) && int(take.size()) < kMaxPassOps;
+            if (ok && nondiag(gi) && g.t >= L && !(high & bitq(g.t))) {
+                if (nh < cap) {
+                    high |= bitq(g.t);
+                    ++nh;
+                } else {
+                    ok = false;
+                }
+            }
+            if (ok) {
+                take.push_back(gi);
+            } else {
+                keep.push_back(gi);
+                defN |= N;
+                defA |= A;
+            }
+        }
+        for (int q = L; q < M && nh < cap; ++q)
+            if (!(high & bitq(q))) {
+                high |= bitq(q);
+                ++nh;
+            }
+        const uint64_t S = (bitq(L) - 1) | high;
+        TilePassDesc d{};
+        int loc[64];
+        for (int q = 0; q < 64; ++q) loc[q] = -1;
+        while (d.L < M && (S & bitq(d.L))) {
+            loc[d.L] = d.L;
+            ++d.L;
+        }
+        for (int q = d.L; q < M; ++q) {
+            if (S & bitq(q)) {
+                loc[q] = d.L + d.nh;
+                d.hpos[d.nh++] = q;
+            } else {
+                d.opos[d.nout++] = q;
+            }
+        }
+        d.b = d.L + d.nh;
+        d.op_begin = int(p->ops.size());
+        d.op_count = int(take.size());
+        for (int gi : take) {
+            const Gate &g = gates[gi];
+            TrajOp op{};
+            std::memcpy(op.U, g.U, sizeof op.U);
+            std::memcpy(op.ax, ax + 3 * gi, sizeof op.ax);
+            op.gate = gi;
+            for (int c = 0; c < g.nc; ++c) {
+                if (S & bitq(g.c[c])) op.lmask |= 1u << loc[g.c[c]];
+                else op.gmask |= bitq(g.c[c]);
+            }
+            const Kind k = kind[gi];
+            if (S & bitq(g.t)) {
+                op.kind = k;
+                op.tl = uint32_t(loc[g.t]);
+            } else {
+                op.kind = K_SCALE;  // diagonal gate (with or without its z error) on an outside qubit
+                op.gsel = bitq(g.t);
+            }
+            p->ops.push_back(op);
+        }
+        p->passes.push_back(d);
+        rem.swap(keep);
+    }
+    return QSIM_OK;
 }
+
+int upload_tables(qsim_traj_plan *p) {
+    if (p->d_passes) cudaFree(p->d_passes);
+    if (p->d_ops) cudaFree(p->d_ops);
+    p->d_passes = nullptr;
+    p->d_ops = nullptr;
+    QS_CUDA(cudaMalloc(&p->d_passes, p->passes.size() * sizeof(TilePassDesc)));
+    QS_CUDA(cudaMemcpy(p->d_passes, p->passes.data(), p->passes.size() * sizeof(TilePassDesc),
+                       cudaMemcpyHostToDevice));
+    if (!p->ops.empty()) {
+        QS_CUDA(cudaMalloc(&p->d_ops, p->ops.size() * sizeof(TrajOp)));
+        QS_CUDA(cudaMemcpy(p->d_ops, p->ops.data(), p->ops.size() * sizeof(TrajOp), cudaMemcpyHostToDevice));
+    }
+    return QSIM_OK;
+}
+
+int launch_traj(qsim_traj_plan *p, int T) {
+    QS_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), p->stream));
+    k_trajectories<<<p->grid, kTrajThreads, p->smem, p->stream>>>(p->M, int(p->passes.size()), p->d_passes, p->d_ops,
+                                                                  p->d_eps, p->n, T, p->d_ideal, p->d_work, p->d_F,
+                                                                  p->d_counter);
+    QS_CHECK_LAUNCH("trajectory kernel launch");
+    return QSIM_OK;
+}
+
+int set_tile_bits(qsim_traj_plan *p, const std::vector<Gate> &gates, const double *ax, int b) {
+    p->tile_bits = std::min(b, p->M);
+    if (int rc = build_passes(p, gates, ax, p->tile_bits)) return rc;
+    if (int rc = upload_tables(p)) return rc;
+    p->smem = (size_t(1) << p->tile_bits) * sizeof(float2);
+    QS_CUDA(cudaFuncSetAttribute(k_trajectories, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    return QSIM_OK;
+}
+
+std::mutex g_tune_mu;
+std::map<std::vector<double>, int> g_tune_cache;  // (M, gates, axes) -> tile bits
+
+}  // namespace
+
+extern "C" {
+
+int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis, size_t n, int max_T,
+                          const qsim_traj_opts *opts, qsim_traj_plan **out) {
+    if (!out) { set_error("out is NULL"); return QSIM_EINVAL; }
+    if (M < 1 || M > 20) { set_error("trajectories: M = %d outside [1, 20]", M); return QSIM_EINVAL; }
+    if (max_T < 1) { set_error("trajectories: max_T must be >= 1"); return QSIM_EINVAL; }
+    if (n > 0 && (!ideal || !err_axis)) { set_error("gates or axes NULL"); return QSIM_EINVAL; }
+    qsim_traj_opts o{};
+    if (opts) o = *opts;
+    if (o.fuse_k < 0 || o.fuse_k > 5) { set_error("fuse_k %d outside [0, 5]", o.fuse_k); return QSIM_EINVAL; }
+    std::vector<Gate> gates(n);
+    for (size_t i = 0; i < n; ++i) {
+        if (int rc = make_gate(M, ideal[i].U, ideal[i].target, ideal[i].controls, ideal[i].ncontrols, &gates[i])) {
+            char msg[512];
+            snprintf(msg, sizeof msg, "gate %zu: %s", i, qsim_last_error());
+            set_error("%s", msg);
+            return rc;
+        }
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(err_axis[3 * i + k])) { set_error("axis %zu not finite", i); return QSIM_EINVAL; }
+    }
+    qsim_traj_plan *p = new qsim_traj_plan();
+    p->M = M;
+    p->n = int(n);
+    p->max_T = max_T;
+    p->use_graph = o.use_graph;
+    int rc = QSIM_OK;
+    auto fail = [&](int code) {
+        qsim_traj_plan_destroy(p);
+        return code;
+    };
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "stream"));
+    }
+    // error-free state: the ordinary tiled path from |0...0>
+    {
+        qsim_state *st = nullptr;
+        if ((rc = qsim_alloc(M, QSIM_C64, &st))) return fail(rc);
+        p->d_ideal = static_cast<float2 *>(st->amps);
+        st->owned = false;  // the plan keeps the amplitudes
+        qsim_opts po{QSIM_MODE_TILED, 0, 0, 0};
+        rc = qsim_apply_circuit(st, ideal, n, &po);
+        qsim_free(st);
+        if (rc) return fail(rc);
+    }
+    int per_sm = 2;
+    p->grid = num_sms() * per_sm;
+    if (p->grid > max_T) p->grid = max_T;
+    {
+        cudaError_t e = cudaMalloc(&p->d_work, (size_t(p->grid) << M) * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_eps, size_t(max_T) * std::max<size_t>(n, 1) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_F, size_t(max_T) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMallocHost(&p->h_eps, size_t(max_T) * std::max<size_t>(n, 1) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMallocHost(&p->h_F, size_t(max_T) * sizeof(double));
+        if (e != cudaSuccess) return fail(cuda_fail(e, "trajectory buffers"));
+    }
+    // tile size: given, or the fastest candidate on a short batch (cached)
+    std::vector<double> key;
+    key.push_back(M);
+    for (size_t i = 0; i < n; ++i) {
+        key.insert(key.end(), ideal[i].U, ideal[i].U + 8);
+        key.push_back(ideal[i].target);
+        key.push_back(ideal[i].ncontrols);
+        key.push_back(ideal[i].controls[0]);
+        key.push_back(ideal[i].controls[1]);
+        key.insert(key.end(), err_axis + 3 * i, err_axis + 3 * i + 3);
+    }
+    int best = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) best = it->second;
+    }
+    if (best == 0) {
+        const int cands[] = {10, 11, 12, 13};
+        float best_ms = 1e30f;
+        const int Tt = std::min(max_T, p->grid);
+        cudaMemsetAsync(p->d_eps, 0, size_t(Tt) * std::max<size_t>(n, 1) * sizeof(double), p->stream);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int b : cands) {
+            if (b > M && b != cands[0]) continue;
+            if ((rc = set_tile_bits(p, gates, err_axis, b))) break;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == QSIM_OK; ++rep) {
+                cudaEventRecord(e0, p->stream);
+                rc = launch_traj(p, Tt);
+                cudaEventRecord(e1, p->stream);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) rc = cuda_fail(e, "tuning run");
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rc) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = std::min(b, M);
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return fail(rc);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    if ((rc = set_tile_bits(p, gates, err_axis, best))) return fail(rc);
+    *out = p;
+    return QSIM_OK;
+}
+
+int qsim_traj_plan_run(qsim_traj_plan *p, const double *eps, int T, double *F_out, double *mean, double *var) {
+    if (!p) { set_error("plan is NULL"); return QSIM_EINVAL; }
+    if (T < 1 || T > p->max_T) { set_error("T = %d outside [1, %d]", T, p->max_T); return QSIM_EINVAL; }
+    if (p->n > 0 && !eps) { set_error("eps is NULL"); return QSIM_EINVAL; }
+    const size_t ne = size_t(T) * size_t(p->n);
+    if (ne) std::memcpy(p->h_eps, eps, ne * sizeof(double));
+    auto enqueue = [&]() -> int {
+        if (ne) QS_CUDA(cudaMemcpyAsync(p->d_eps, p->h_eps, ne * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        if (int rc = launch_traj(p, T)) return rc;
+        QS_CUDA(cudaMemcpyAsync(p->h_F, p->d_F, size_t(T) * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        return QSIM_OK;
+    };
+    if (p->use_graph) {
+        if (!p->gexec || p->graph_T != T) {
+            if (p->gexec) cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+            QS_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue();
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "trajectory graph capture");
+            e = cudaGraphInstantiate(&p->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "trajectory graph instantiate");
+            p->graph_T = T;
+        }
+        QS_CUDA(cudaGraphLaunch(p->gexec, p->stream));
+    } else {
+        if (int rc = enqueue()) return rc;
+    }
+    QS_CUDA(cudaStreamSynchronize(p->stream));
+    double s = 0.0;
+    for (int t = 0; t < T; ++t) s += p->h_F[t];
+    const double mu = s / T;
+    double v = 0.0;
+    for (int t = 0; t < T; ++t) v += (p->h_F[t] - mu) * (p->h_F[t] - mu);
+    if (F_out) std::memcpy(F_out, p->h_F, size_t(T) * sizeof(double));
+    if (mean) *mean = mu;
+    if (var) *var = T > 1 ? v / (T - 1) : 0.0;
+    return QSIM_OK;
+}
+
+int qsim_traj_plan_info(const qsim_traj_plan *p, int *tile_bits, int *n_passes, int *grid) {
+    if (!p) { set_error("plan is NULL"); return QSIM_EINVAL; }
+    if (tile_bits) *tile_bits = p->tile_bits;
+    if (n_passes) *n_passes = int(p->passes.size());
+    if (grid) *grid = p->grid;
+    return QSIM_OK;
+}
+
+void qsim_traj_plan_destroy(qsim_traj_plan *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    cudaFree(p->d_passes);
+    cudaFree(p->d_ops);
+    cudaFree(p->d_ideal);
+    cudaFree(p->d_work);
+    cudaFree(p->d_eps);
+    cudaFree(p->d_F);
+    cudaFree(p->d_counter);
+    if (p->h_eps) cudaFreeHost(p->h_eps);
+    if (p->h_F) cudaFreeHost(p->h_F);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+int qsim_run_trajectories(int M, const qsim_gate *ideal, const double *err_axis, size_t n, const double *eps, int T,
+                          const qsim_traj_opts *opts, double *F_out, double *mean, double *var) {
+    qsim_traj_plan *p = nullptr;
+    if (int rc = qsim_traj_plan_create(M, ideal, err_axis, n, T, opts, &p)) return rc;
+    int rc = qsim_traj_plan_run(p, eps, T, F_out, mean, var);
+    qsim_traj_plan_destroy(p);
+    return rc;
+}
+
+}  // extern "C"

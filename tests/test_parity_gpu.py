@@ -344,6 +344,25 @@ def test_fused_qft_and_brickwork(orc, k):
     _fused_case(orc, M, b["noisy"], k, x)
 
 
+def test_fused_non_unitary_block(orc):
+    """A non-unitary block is applied as given (no norm correction)."""
+    M = 14
+    rng = np.random.default_rng(91)
+    recs = []
+    for _ in range(12):
+        U = (rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))) * 0.7
+        recs.append(W.gate_record(U, int(rng.integers(0, 4)), ()))
+    x, x128 = _input(M, "c64")
+    ref = orc.run(M, W._pack(recs), x128)
+    ref_scale = np.abs(ref).max()
+    plan = qs.Plan(M, W._pack(recs), mode="fused", fuse_k=4)
+    st = qs.State(M).set(x)
+    plan.execute(st)
+    plan.status()
+    got = st.get().astype(np.complex128)
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, ref_scale)
+
+
 def test_fused_out_of_place(orc):
     import torch
     M = 16
