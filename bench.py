@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the single-gate, batched-trajectory and serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -312,6 +315,14 @@ def run_ours(args, rank, world, local):
                          "ms_per_step": dt * 1e3, "h2d_bytes_per_step": int(x.nbytes),
                          "d2h_bytes_per_step": 24, "steps": ke}
 
+    if not args.no_extras:
+        del xin, ideal, noisy, p_ideal, p_noisy
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        result["single_gate"] = bench_single_gate(stream)
+        result["batched"] = bench_trajectories(world)
+        result["serving"] = bench_serving(args.serve_requests, world)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, ng, dt, nt = oracle_sample(M, c["noisy"], x, budget_s=15.0)
         result["cpu_baseline"] = {"value": v, "unit": "amp-updates/s", "cores": nt, "kind": "oracle",
@@ -319,6 +330,148 @@ def run_ours(args, rank, world, local):
                                             f"(complex128), {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(result), flush=True)
+
+
+# ------------------------------------------------------------------ extras ---
+def _events_ms(fn, reps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_single_gate(stream):
+    """One dense gate per launch (k_gate_*) on an M=30 complex64 state (8 GiB):
+    algorithmic bytes 16 * 2^30 per launch; targets below and above the
+    512-byte warp chunk."""
+    import torch
+    import paper_quant_ph_9804039_gb300 as qs
+    from workloads import generators as W
+    M = 30
+    st = qs.State(M, stream=stream)
+    U = W.mat_haar_su2(np.random.default_rng(9))
+    peak, _ = measured_peaks()
+    out = {"M": M, "bytes_per_launch": 16 << M, "targets": {}}
+    for t in (0, 3, 7, 20, 29):
+        ms = _events_ms(lambda: st.apply_gate(U, t), 5, stream)
+        gbs = (16 << M) / (ms / 1e3) / 1e9
+        out["targets"][str(t)] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    ms = _events_ms(lambda: st.apply_gate(W.mat_x(), 17, (25,)), 5, stream)
+    out["cnot_17_ctl25"] = {"ms": round(ms, 4), "GB/s": round((8 << M) / (ms / 1e3) / 1e9, 1)}
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_trajectories(world):
+    """Batched error trajectories: M=16, T=4096, 20-layer brickwork, sigma=5e-3,
+    one persistent launch replayed from a CUDA graph; against running the
+    same trajectories one circuit at a time, one gate per launch."""
+    import paper_quant_ph_9804039_gb300 as qs
+    from workloads import generators as W
+    M, T = 16, 4096
+    b = W.circuit_brickwork(M, 20)
+    eps = W.trajectory_eps(len(b["ideal"]), T, 5e-3)
+    plan = qs.TrajPlan(M, b["ideal"], b["axes"], max_T=T, use_graph=True)
+    plan.run(eps)
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        F, mean, var = plan.run(eps)
+    dt = (time.perf_counter() - t0) / reps
+    # sequential one-gate-per-launch form on a sample of trajectories
+    ideal = qs.State(M)
+    qs.Plan(M, b["ideal"], mode="unfused").execute(ideal)
+    noisy = qs.State(M)
+    ns = 16
+    t0 = time.perf_counter()
+    for t in range(ns):
+        rec = W.with_errors(b["ideal"], b["axes"], eps[t])
+        noisy.reset()
+        qs.Plan(M, rec, mode="unfused").execute(noisy)
+        qs.fidelity(ideal, noisy)
+    dts = (time.perf_counter() - t0) / ns
+    info = plan.info()
+    return {"workload": "brickwork-m16-t4096", "trajectories_per_s": world * T / dt, "s_per_batch": dt,
+            "mean_F": mean, "var_F": var, "tile_bits": info["tile_bits"], "passes": info["n_passes"],
+            "grid": info["grid"], "gates": int(len(b["ideal"])),
+            "amp_updates_per_s": world * T * len(b["ideal"]) * float(1 << M) / dt,
+            "sequential_unfused_trajectories_per_s": 1.0 / dts,
+            "sequential_sample": f"{ns} trajectories, errors applied on the host, one gate per launch"}
+
+
+def bench_serving(n_requests, world):
+    """Served stream: Poisson arrivals, M ~ U{12..26}, 50..500 gates, sigma
+    log-uniform in [1e-5, 1e-2], 160 GiB budget.  The offered rate is the
+    measured capacity of the sequential one-gate-per-launch loop (load 1.0
+    for it).  Latency = completion - arrival.  The sequential loop serves a
+    sample of the same stream live (one request at a time, in arrival order);
+    the continuous-batching server serves the whole stream."""
+    import paper_quant_ph_9804039_gb300 as qs
+    from workloads import generators as W
+    reqs = W.serving_requests(n_requests)
+    circs = [W.request_circuit(r) for r in reqs]
+
+    def serve_one(r, c):
+        a = qs.State(r["M"])
+        b = qs.State(r["M"])
+        qs.Plan(r["M"], c["ideal"], mode="unfused").execute(a)
+        qs.Plan(r["M"], c["noisy"], mode="unfused").execute(b)
+        return qs.fidelity(a, b)
+
+    serve_one(reqs[0], circs[0])
+    t0 = time.perf_counter()
+    ncal = min(len(reqs), 50)
+    for r, c in zip(reqs[:ncal], circs[:ncal]):
+        serve_one(r, c)
+    lam = ncal / (time.perf_counter() - t0)  # sequential capacity, requests/s
+    # sequential loop under the stream (sample)
+    ns = min(len(reqs), 200)
+    seq_lat = []
+    t_start = time.perf_counter()
+    t_arr = 0.0
+    for r, c in zip(reqs[:ns], circs[:ns]):
+        t_arr += r["gap"] / lam
+        now = time.perf_counter() - t_start
+        if now < t_arr:
+            time.sleep(t_arr - now)
+        serve_one(r, c)
+        seq_lat.append(time.perf_counter() - t_start - t_arr)
+    seq_rate = ns / (time.perf_counter() - t_start)
+    # the continuous-batching server under the whole stream
+    srv = qs.Server(hbm_budget=160 << 30, max_slots=16, mode="tiled")
+    t_start = time.perf_counter()
+    t_arr = 0.0
+    arrival = {}
+    done = []
+    for r, c in zip(reqs, circs):
+        t_arr += r["gap"] / lam
+        while time.perf_counter() - t_start < t_arr:
+            done += srv.poll(256, wait_ms=0)
+            time.sleep(0.0002)
+        rid = srv.submit(r["M"], c["ideal"], c["noisy"])
+        arrival[rid] = time.perf_counter()
+    while len(done) < len(reqs):
+        done += srv.poll(256, wait_ms=100)
+    t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([d["t_done"] - d["t_submit"] for d in done])
+    ok = sum(1 for d in done if d["status"] == 0)
+    return {"workload": "served-stream", "requests": len(reqs), "ok": ok, "offered_rate": lam,
+            "requests_per_s": world * len(reqs) / (t_end - t_start),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_active": st["max_active"], "peak_state_bytes": st["peak_bytes"],
+            "sequential_unfused": {"requests_per_s": seq_rate, "sample": ns,
+                                   "p50_ms": float(np.percentile(seq_lat, 50) * 1e3),
+                                   "p99_ms": float(np.percentile(seq_lat, 99) * 1e3)}}
 
 
 # ---------------------------------------------------------- reference arm ---

@@ -71,6 +71,34 @@ inline uint64_t bit(int q) { return uint64_t(1) << q; }
 
 int default_tile_bits(qsim_prec prec) { return prec == QSIM_C64 ? 12 : 11; }
 
+// Enumeration spec: the amplitudes (diagonal kinds) or pairs (pair kinds) an
+// op touches are the tile indices with the listed bits inserted.
+template <typename T2>
+void set_enum(TileOp<T2> &op, int tpos, bool t_insert, bool t_value, uint32_t lmask) {
+    int pos[4], val[4], n = 0;
+    if (t_insert) {
+        pos[n] = tpos;
+        val[n++] = t_value ? 1 : 0;
+    }
+    for (int q = 0; q < 32; ++q)
+        if (lmask & (1u << q)) {
+            pos[n] = q;
+            val[n++] = 1;
+        }
+    for (int a = 0; a < n; ++a)
+        for (int b = a + 1; b < n; ++b)
+            if (pos[b] < pos[a]) {
+                std::swap(pos[a], pos[b]);
+                std::swap(val[a], val[b]);
+            }
+    op.npos = uint8_t(n);
+    op.posval = 0;
+    for (int a = 0; a < n; ++a) {
+        op.pos[a] = uint8_t(pos[a]);
+        op.posval |= uint8_t(val[a] << a);
+    }
+}
+
 template <typename T2>
 TileOp<T2> make_tile_op(const Gate &g, const int *loc, uint64_t S) {
     TileOp<T2> op{};
@@ -96,6 +124,12 @@ TileOp<T2> make_tile_op(const Gate &g, const int *loc, uint64_t S) {
     if (S & bit(g.t)) {
         op.kind = g.kind;
         op.tl = uint32_t(loc[g.t]);
+        if (g.kind == K_DENSE || g.kind == K_SWAPX)
+            set_enum(op, loc[g.t], true, false, op.lmask);  // pairs: target 0, controls 1
+        else if (g.kind == K_PHASE1)
+            set_enum(op, loc[g.t], true, true, op.lmask);  // only target-1 states change
+        else
+            set_enum(op, 0, false, false, op.lmask);  // K_DIAG: every state with the controls set
     } else {  // diagonal gate on a qubit outside the tile: one factor per tile
         op.kind = K_SCALE;
         if (g.kind == K_PHASE1) {  // only tiles with the target bit set change
@@ -106,8 +140,52 @@ TileOp<T2> make_tile_op(const Gate &g, const int *loc, uint64_t S) {
         } else {
             op.gsel = bit(g.t);
         }
+        set_enum(op, 0, false, false, op.lmask);
     }
     return op;
+}
+
+// Pre-phase table of a run of phase gates (all qubits inside the tile) that
+// precedes an uncontrolled dense gate on local target tl: entry
+// (idx << 1) | target bit, idx over the local bits tpos[0..tw).  FP64
+// products, stored as float hi + lo (complex64) or double (complex128).
+template <typename T2>
+uint32_t add_pre_table(std::vector<unsigned char> &runs, const std::vector<Gate> &gates, const std::vector<int> &run,
+                       const int *loc, int tl, const int *tpos, int tw, bool *one0) {
+    const int ne = 1 << (tw + 1);
+    const size_t esz = sizeof(T2) == 8 ? 16 : 16;
+    const size_t start = (runs.size() + 15) & ~size_t(15);
+    runs.resize(start + size_t(ne) * esz, 0);
+    *one0 = true;
+    for (int e = 0; e < ne; ++e) {
+        uint32_t lb = (e & 1) ? (1u << tl) : 0u;  // local bits of this entry
+        for (int k = 0; k < tw; ++k)
+            if ((e >> (k + 1)) & 1) lb |= 1u << tpos[k];
+        double fr = 1.0, fi = 0.0;
+        for (int gi : run) {
+            const Gate &g = gates[gi];
+            bool on = true;
+            for (int c = 0; c < g.nc; ++c) on = on && ((lb >> loc[g.c[c]]) & 1);
+            if (!on) continue;
+            const bool up = (lb >> loc[g.t]) & 1;
+            const double ur = up ? g.U[6] : g.U[0], ui = up ? g.U[7] : g.U[1];
+            const double nr = fr * ur - fi * ui, ni = fr * ui + fi * ur;
+            fr = nr;
+            fi = ni;
+        }
+        if (!(e & 1) && !(fr == 1.0 && fi == 0.0)) *one0 = false;
+        unsigned char *dst = runs.data() + start + size_t(e) * esz;
+        if constexpr (sizeof(T2) == 8) {
+            float v[4];
+            split_f(fr, v[0], v[2]);
+            split_f(fi, v[1], v[3]);
+            std::memcpy(dst, v, 16);
+        } else {
+            const double v[2] = {fr, fi};
+            std::memcpy(dst, v, 16);
+        }
+    }
+    return uint32_t(start);
 }
 
 constexpr int kMinPhaseRun = 6;  // shorter runs of phase gates are applied one by one
@@ -272,17 +350,53 @@ void plan_tiled(qsim_plan *p, int b_req, std::vector<TileOp<T2>> &ops, std::vect
         for (size_t i = 0; i < seq.size();) {
             size_t j = i;
             while (j < seq.size() && is_phase_gate(p->gates[seq[j]])) ++j;
-            if (j - i >= size_t(kMinPhaseRun)) {
+            if (j == i) {  // a non-phase gate
+                ops.push_back(make_tile_op<T2>(p->gates[seq[i]], loc, S));
+                ++i;
+                continue;
+            }
+            const std::vector<int> run(seq.begin() + i, seq.begin() + j);
+            // a run followed by an uncontrolled dense gate, all inside the tile
+            // and over at most 8 other local bits, rides on that gate
+            if (j < seq.size() && p->gates[seq[j]].kind == K_DENSE && p->gates[seq[j]].nc == 0) {
+                const int tl = loc[p->gates[seq[j]].t];
+                uint32_t bits = 0;
+                bool inside = true;
+                for (int gi : run) {
+                    const Gate &g = p->gates[gi];
+                    inside = inside && (S & bit(g.t));
+                    for (int c = 0; c < g.nc; ++c) inside = inside && (S & bit(g.c[c]));
+                    if (!inside) break;
+                    bits |= 1u << loc[g.t];
+                    for (int c = 0; c < g.nc; ++c) bits |= 1u << loc[g.c[c]];
+                }
+                bits &= ~(1u << tl);
+                if (inside && tl >= 0 && __builtin_popcount(bits) <= 8) {
+                    TileOp<T2> op = make_tile_op<T2>(p->gates[seq[j]], loc, S);
+                    int tpos[8], tw = 0;
+                    for (int q = 0; q < 32; ++q)
+                        if (bits & (1u << q)) tpos[tw++] = q;
+                    bool one0 = false;
+                    if (runs.empty()) runs.resize(16, 0);  // offset 0 means "no table"
+                    op.tab_off = add_pre_table<T2>(runs, p->gates, run, loc, tl, tpos, tw, &one0);
+                    op.tw = uint8_t(tw);
+                    op.tflags = one0 ? 1 : 0;
+                    for (int k = 0; k < tw; ++k) op.tpos[k] = uint8_t(tpos[k]);
+                    ops.push_back(op);
+                    i = j + 1;
+                    continue;
+                }
+            }
+            if (run.size() >= size_t(kMinPhaseRun)) {
                 TileOp<T2> op{};
                 op.kind = K_PHRUN;
-                op.gsel = add_phase_run<TurnT<T2>>(runs, p->gates, std::vector<int>(seq.begin() + i, seq.begin() + j),
-                                                   M, pos, d.b);
+                if (runs.empty()) runs.resize(16, 0);
+                op.gsel = add_phase_run<TurnT<T2>>(runs, p->gates, run, M, pos, d.b);
                 ops.push_back(op);
-                i = j;
             } else {
-                if (j == i) j = i + 1;
-                for (; i < j; ++i) ops.push_back(make_tile_op<T2>(p->gates[seq[i]], loc, S));
+                for (int gi : run) ops.push_back(make_tile_op<T2>(p->gates[gi], loc, S));
             }
+            i = j;
         }
         d.op_count = int(ops.size()) - d.op_begin;
         st.bytes = 2.0 * std::ldexp(1.0, M) * double(amp_bytes(p->prec));

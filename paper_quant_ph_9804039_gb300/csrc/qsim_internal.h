@@ -87,15 +87,27 @@ struct TilePassDesc {
 
 template <typename T2>
 struct TileOp {
-    T2 u[4];          // U00, U01, U10, U11 in the state precision (hi parts for complex64)
-    T2 ul[4];         // lo parts (complex64; zero for complex128)
-    uint32_t kind;    // Kind
-    uint32_t tl;      // target position inside the tile (K_SCALE: unused)
-    uint32_t lmask;   // control bits inside the tile (tile-local positions)
-    uint32_t pad;
-    uint64_t gmask;   // control bits outside the tile (global positions)
-    uint64_t gsel;    // K_SCALE: global target bit
+    T2 u[4];           // U00, U01, U10, U11 in the state precision (hi parts for complex64)
+    T2 ul[4];          // lo parts (complex64; zero for complex128)
+    uint32_t kind;     // Kind
+    uint32_t tl;       // target position inside the tile (K_SCALE: unused)
+    uint32_t lmask;    // control bits inside the tile (tile-local positions)
+    uint32_t tab_off;  // K_DENSE: byte offset of a pre-phase table in the run buffer (0 = none)
+    uint64_t gmask;    // control bits outside the tile (global positions)
+    uint64_t gsel;     // K_SCALE: global target bit; K_PHRUN: byte offset of the record
+    uint8_t npos;      // bits inserted to enumerate the touched amplitudes (or pairs)
+    uint8_t pos[3];    // their tile-local positions, ascending
+    uint8_t posval;    // bit k: the value inserted at pos[k]
+    uint8_t tw;        // pre-phase table: index bits besides the target
+    uint8_t tflags;    // bit 0: the table's target-0 entries are all exactly one
+    uint8_t pad;
+    uint8_t tpos[8];   // tile-local positions of the table's index bits
 };
+static_assert(sizeof(TileOp<float2>) % 16 == 0 && sizeof(TileOp<double2>) % 16 == 0, "ops are copied in 16-byte units");
+// A pre-phase table holds, for every value of (tpos bits, target bit), the
+// product of the diagonal factors of a run of phase gates that precedes an
+// uncontrolled dense gate in a pass: entry (idx << 1) | target.  complex64:
+// float4 (hi.re, hi.im, lo.re, lo.im) per entry; complex128: double2.
 
 // A run of diagonal gates diag(e^{i a}, e^{i b}) with at most one control
 // multiplies amplitude g by e^{i Phi(g)}, Phi a quadratic polynomial of the
@@ -114,6 +126,7 @@ using TurnT = typename std::conditional<sizeof(T2) == 8, uint32_t, uint64_t>::ty
 
 int launch_tile_pass(void *dst, const void *src, int M, qsim_prec prec, const TilePassDesc &d,
                      const void *ops_dev, const void *runs_dev, cudaStream_t s);
+constexpr int kTileOpSmemBytes = 24 * 1024;  // a pass's ops are staged in shared memory up to this size
 int tile_max_bits(qsim_prec prec);
 int tile_prepare(qsim_prec prec);  // one-time kernel attributes (call before any stream capture)
 
