@@ -22,81 +22,15 @@
 namespace qs {
 namespace {
 
-template <typename Turn>
-struct RunSmem {
-    Turn cl[16];       // per-tile linear coefficient of each tile-local bit
-    Turn lin_lo[128];  // linear part over local bits [0, 7)
-    Turn lin_hi[128];  // linear part over local bits [7, b)
-    Turn kt;           // constant of the tile
-};
-
-// e^{2 pi i phi / 2^32}: the top 24 bits go through sincospif (exact argument),
-// the low 8 bits (< 3.7e-7 rad) as a first-order rotation.
-__device__ __forceinline__ float2 expi_turns(uint32_t phi) {
-    const int32_t sp = int32_t(phi);
-    const float x = float(sp >> 8) * (1.0f / 8388608.0f);  // (phi >> 8) / 2^23, in [-1, 1)
-    float sn, cs;
-    sincospif(x, &sn, &cs);
-    const float r = float(phi & 255u) * 1.4629180792671596e-09f;  // 2 pi / 2^32
-    return make_float2(fmaf(-sn, r, cs), fmaf(cs, r, sn));
-}
-// e^{2 pi i phi / 2^64}
-__device__ __forceinline__ double2 expi_turns(uint64_t phi) {
-    const double x = double(int64_t(phi)) * (1.0 / 9223372036854775808.0);
-    double sn, cs;
-    sincospi(x, &sn, &cs);
-    return make_double2(cs, sn);
-}
-
 template <typename T2>
 __device__ void tile_phase_run(T2 *s, int n, const TilePassDesc &d, uint64_t tile,
                                const unsigned char *__restrict__ rec, RunSmem<TurnT<T2>> &rs) {
     using Turn = TurnT<T2>;
-    const PhaseRunHdr h = *reinterpret_cast<const PhaseRunHdr *>(rec);
-    const int M = int(h.M);
-    const Turn *c0p = reinterpret_cast<const Turn *>(rec + sizeof(PhaseRunHdr));
-    const Turn *c = c0p + 1;
-    const Turn *w = c + M;
-    const Turn *Q = reinterpret_cast<const Turn *>(rec + h.q_offset);
-    const int b = d.b;
-    const int t = threadIdx.x;
-    if (t < b) {  // linear coefficient of local bit t, given the tile's outside bits
-        const int q = t < d.L ? t : d.hpos[t - d.L];
-        Turn v = c[q];
-        for (int k = 0; k < d.nout; ++k)
-            if ((tile >> k) & 1) v += w[q * M + d.opos[k]];
-        rs.cl[t] = v;
-    } else if (t == 32) {  // constant of the tile
-        Turn v = *c0p;
-        for (int k = 0; k < d.nout; ++k) {
-            if (!((tile >> k) & 1)) continue;
-            const int r = d.opos[k];
-            v += c[r];
-            for (int k2 = k + 1; k2 < d.nout; ++k2)
-                if ((tile >> k2) & 1) v += w[r * M + d.opos[k2]];
-        }
-        rs.kt = v;
-    }
-    __syncthreads();
-    const int bl = b < 7 ? b : 7;
-    const int bh = b - bl;
-    if (t < (1 << bl)) {
-        Turn v = 0;
-        for (int j = 0; j < bl; ++j)
-            if ((t >> j) & 1) v += rs.cl[j];
-        rs.lin_lo[t] = v;
-    }
-    if (t >= 128 && t - 128 < (1 << bh)) {
-        const int v0 = t - 128;
-        Turn v = 0;
-        for (int j = 0; j < bh; ++j)
-            if ((v0 >> j) & 1) v += rs.cl[bl + j];
-        rs.lin_hi[v0] = v;
-    }
-    __syncthreads();
+    const Turn *Q = phase_run_setup<Turn>(d, tile, rec, rs);
+    const int bl = d.b < 7 ? d.b : 7;
     const Turn kt = rs.kt;
     const uint32_t lomask = (1u << bl) - 1;
-    for (int u = t; u < n; u += blockDim.x) {
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
         const Turn phi = kt + rs.lin_lo[u & lomask] + rs.lin_hi[u >> bl] + __ldg(Q + u);
         s[u] = cmul(expi_turns(phi), s[u]);
     }

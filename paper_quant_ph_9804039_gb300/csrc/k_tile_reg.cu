@@ -1,0 +1,243 @@
+// Tile passes with register rounds (complex64).
+//
+// The tile of a pass (Section 2.1's pair rule restricted to 2^b amplitudes,
+// see k_tile.cu) is split further: a round picks RB of the tile's qubits (its
+// slot qubits) and every one of the block's 256 threads holds, in registers,
+// the 2^RB amplitudes of its index that differ only in those qubits.  Every
+// gate of the round targets a slot qubit, so its pairs lie inside one
+// thread's registers; controls and diagonal gates on any qubit are evaluated
+// from each amplitude's index.  A round costs one load and one store of each
+// amplitude however many gates it holds; the first round of a pass reads
+// device memory and the last writes it, and shared memory carries the tile
+// between rounds.  Runs of phase gates on tile qubits are one table lookup
+// per amplitude (K_TAB), longer runs that reach outside the tile a phase
+// polynomial (K_PHRUN).  Gate entries are hi + lo floats (compensated
+// complex64, see cx.cuh).
+#include "cx.cuh"
+#include "qsim_internal.h"
+#include "tile_ops.cuh"
+
+namespace qs {
+namespace {
+
+constexpr int kThreads = 1 << kRegThreadBits;
+
+template <int RB>
+struct Slots {
+    static constexpr int S = 1 << RB;
+    float2 x[S];
+};
+
+// Pair update on slot bit K: pairs (c, c | 2^K) of this thread's slots.
+template <int RB, int K, bool SWAP>
+__device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op, uint32_t i0, const uint32_t *dep) {
+    constexpr int S = 1 << RB;
+#pragma unroll
+    for (int c = 0; c < S; ++c) {
+        if (c & (1 << K)) continue;
+        const int c1 = c | (1 << K);
+        const uint32_t i = i0 | dep[c];
+        if ((i & op.lmask) != op.lmask) continue;
+        const float2 a = v.x[c], b = v.x[c1];
+        if (SWAP) {
+            v.x[c] = b;
+            v.x[c1] = a;
+        } else {
+            v.x[c] = cmad2x(op.u[0], op.ul[0], a, op.u[1], op.ul[1], b);
+            v.x[c1] = cmad2x(op.u[2], op.ul[2], a, op.u[3], op.ul[3], b);
+        }
+    }
+}
+
+template <int RB, bool SWAP>
+__device__ __forceinline__ void pairs_any(Slots<RB> &v, const RegOp &op, uint32_t i0, const uint32_t *dep) {
+    switch (op.k) {
+        case 0: pairs<RB, 0, SWAP>(v, op, i0, dep); break;
+        case 1: pairs<RB, 1, SWAP>(v, op, i0, dep); break;
+        case 2: pairs<RB, 2, SWAP>(v, op, i0, dep); break;
+        default: if constexpr (RB > 3) pairs<RB, 3, SWAP>(v, op, i0, dep); break;
+    }
+}
+
+template <int RB>
+__device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t i0, const uint32_t *dep,
+                                         uint64_t base, uint64_t tile, const TilePassDesc &d,
+                                         const unsigned char *__restrict__ runs, RunSmem<uint32_t> &rs) {
+    constexpr int S = 1 << RB;
+    switch (op.kind) {
+        case K_DENSE: pairs_any<RB, false>(v, op, i0, dep); break;
+        case K_SWAPX: pairs_any<RB, true>(v, op, i0, dep); break;
+        case K_PHASE1: {
+            const uint32_t m = op.lmask | op.tb;
+#pragma unroll
+            for (int c = 0; c < S; ++c)
+                if (((i0 | dep[c]) & m) == m) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
+            break;
+        }
+        case K_DIAG: {
+#pragma unroll
+            for (int c = 0; c < S; ++c) {
+                const uint32_t i = i0 | dep[c];
+                if ((i & op.lmask) != op.lmask) continue;
+                v.x[c] = (i & op.tb) ? cmulx(op.u[3], op.ul[3], v.x[c]) : cmulx(op.u[0], op.ul[0], v.x[c]);
+            }
+            break;
+        }
+        case K_SCALE: {
+            const bool up = (base & op.gsel) != 0;
+            const float2 f = up ? op.u[3] : op.u[0], fl = up ? op.ul[3] : op.ul[0];
+#pragma unroll
+            for (int c = 0; c < S; ++c)
+                if (((i0 | dep[c]) & op.lmask) == op.lmask) v.x[c] = cmulx(f, fl, v.x[c]);
+            break;
+        }
+        case K_TAB: {
+            uint32_t g = 0;  // index bits held by the thread's base index
+            for (int j = 0; j < op.tw; ++j) g |= ((i0 >> op.tpos[j]) & 1u) << j;
+            const float4 *tab = reinterpret_cast<const float4 *>(runs + op.tab_off);
+#pragma unroll
+            for (int c = 0; c < S; ++c) {
+                if (op.tb && !((i0 | dep[c]) & op.tb)) continue;
+                const float4 t = __ldg(tab + (g | op.cidx[c]));
+                v.x[c] = cmulx(make_float2(t.x, t.y), make_float2(t.z, t.w), v.x[c]);
+            }
+            break;
+        }
+        case K_PHRUN: {
+            const uint32_t *Q = phase_run_setup<uint32_t>(d, tile, runs + op.gsel, rs);
+            const int bl = d.b < 7 ? d.b : 7;
+            const uint32_t lomask = (1u << bl) - 1;
+            const uint32_t kt = rs.kt;
+#pragma unroll
+            for (int c = 0; c < S; ++c) {
+                const uint32_t i = i0 | dep[c];
+                const uint32_t phi = kt + rs.lin_lo[i & lomask] + rs.lin_hi[i >> bl] + __ldg(Q + i);
+                v.x[c] = cmul(expi_turns(phi), v.x[c]);
+            }
+            break;
+        }
+        default: break;
+    }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(kThreads, 2) k_tile_reg(float2 *dst, const float2 *src, TilePassDesc d,
+                                                          const RegOp *__restrict__ ops,
+                                                          const RoundDesc *__restrict__ rounds,
+                                                          const unsigned char *__restrict__ runs, uint64_t ntiles) {
+    constexpr int S = 1 << RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *s = reinterpret_cast<float2 *>(smem_raw);
+    RegOp *sops = reinterpret_cast<RegOp *>(smem_raw + (d.round_count > 1 ? (size_t(1) << d.b) * sizeof(float2) : 0));
+    __shared__ uint64_t hoff[1 << kMaxTileHigh];
+    __shared__ RunSmem<uint32_t> rs;
+    const int tid = threadIdx.x;
+    {  // the pass's ops, staged once
+        const int4 *g4 = reinterpret_cast<const int4 *>(ops + d.op_begin);
+        int4 *s4 = reinterpret_cast<int4 *>(sops);
+        const int n4 = int(d.op_count * sizeof(RegOp) / 16);
+        for (int k = tid; k < n4; k += kThreads) s4[k] = g4[k];
+    }
+    for (int k = tid; k < (1 << d.nh); k += kThreads) {
+        uint64_t off = 0;
+        for (int j = 0; j < d.nh; ++j)
+            if ((k >> j) & 1) off |= uint64_t(1) << d.hpos[j];
+        hoff[k] = off;
+    }
+    __syncthreads();
+    const uint32_t lowmask = (1u << d.L) - 1;
+    Slots<RB> v;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint64_t base = 0;
+        for (int j = 0; j < d.nout; ++j)
+            if ((tile >> j) & 1) base |= uint64_t(1) << d.opos[j];
+        for (int rd = 0; rd < d.round_count; ++rd) {
+            const RoundDesc R = rounds[d.round_begin + rd];
+            uint32_t i0 = uint32_t(tid);
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                const int q = R.pos[k];
+                i0 = ((i0 >> q) << (q + 1)) | (i0 & ((1u << q) - 1));
+            }
+            uint32_t dep[S];
+#pragma unroll
+            for (int c = 0; c < S; ++c) {
+                uint32_t o = 0;
+#pragma unroll
+                for (int k = 0; k < RB; ++k)
+                    if (c & (1 << k)) o |= 1u << R.pos[k];
+                dep[c] = o;
+            }
+            if (rd == 0) {
+#pragma unroll
+                for (int c = 0; c < S; ++c) {
+                    const uint32_t i = i0 | dep[c];
+                    v.x[c] = src[base | hoff[i >> d.L] | (i & lowmask)];
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < S; ++c) v.x[c] = s[i0 | dep[c]];
+            }
+            for (int k = R.op_begin; k < R.op_begin + R.op_count; ++k) {
+                const RegOp &op = sops[k];
+                if ((base & op.gmask) != op.gmask) continue;  // uniform over the block
+                apply_op<RB>(v, op, i0, dep, base, tile, d, runs, rs);
+            }
+            if (rd + 1 == d.round_count) {
+#pragma unroll
+                for (int c = 0; c < S; ++c) {
+                    const uint32_t i = i0 | dep[c];
+                    dst[base | hoff[i >> d.L] | (i & lowmask)] = v.x[c];
+                }
+            } else {
+                __syncthreads();  // every thread has read its amplitudes of the previous round
+#pragma unroll
+                for (int c = 0; c < S; ++c) s[i0 | dep[c]] = v.x[c];
+                __syncthreads();
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int tile_reg_prepare() {
+    static int configured[64];
+    int dev = 0;
+    QS_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && configured[dev]) return QSIM_OK;
+    QS_CUDA(cudaFuncSetAttribute(k_tile_reg<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + kTileOpSmemBytes));
+    QS_CUDA(cudaFuncSetAttribute(k_tile_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + kTileOpSmemBytes));
+    if (dev < 64) configured[dev] = 1;
+    return QSIM_OK;
+}
+
+int launch_tile_reg(void *dst, const void *src, int M, const TilePassDesc &d, const void *ops_dev,
+                    const void *rounds_dev, const void *runs_dev, cudaStream_t s) {
+    const int RB = d.b - kRegThreadBits;
+    if (RB < 3 || RB > 4) {
+        set_error("register rounds need a tile of %d..%d qubits", kRegThreadBits + 3, kRegThreadBits + 4);
+        return QSIM_EINVAL;
+    }
+    if (int rc = tile_reg_prepare()) return rc;
+    const uint64_t ntiles = uint64_t(1) << (M - d.b);
+    const size_t smem = (d.round_count > 1 ? (size_t(1) << d.b) * sizeof(float2) : 0) + size_t(d.op_count) * sizeof(RegOp);
+    int per_sm = int((220 * 1024) / (smem + 6144));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2048 / kThreads) per_sm = 2048 / kThreads;
+    uint64_t grid = uint64_t(num_sms()) * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    const RegOp *ops = static_cast<const RegOp *>(ops_dev);
+    const RoundDesc *rounds = static_cast<const RoundDesc *>(rounds_dev);
+    const unsigned char *runs = static_cast<const unsigned char *>(runs_dev);
+    if (RB == 3)
+        k_tile_reg<3><<<unsigned(grid), kThreads, smem, s>>>(static_cast<float2 *>(dst), static_cast<const float2 *>(src),
+                                                             d, ops, rounds, runs, ntiles);
+    else
+        k_tile_reg<4><<<unsigned(grid), kThreads, smem, s>>>(static_cast<float2 *>(dst), static_cast<const float2 *>(src),
+                                                             d, ops, rounds, runs, ntiles);
+    QS_CHECK_LAUNCH("register tile pass launch");
+    return QSIM_OK;
+}
+
+}  // namespace qs

@@ -46,6 +46,10 @@ struct qsim_plan {
     size_t runs_bytes = 0;
     void *d_rimg = nullptr;  // R_hi / R_lo images of the fused blocks
     size_t rimg_bytes = 0;
+    void *d_regops = nullptr;  // register-round ops and rounds of the complex64 tile passes
+    size_t regops_bytes = 0;
+    void *d_rounds = nullptr;
+    size_t rounds_bytes = 0;
     int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
     int fuse_k = 0;
     // non-null: device tables are allocated and freed stream-ordered on this
@@ -279,6 +283,145 @@ size_t add_phase_run(std::vector<unsigned char> &runs, const std::vector<Gate> &
         Q[u] = v;
     }
     return start;
+}
+
+// ------------------------------------------------------- register rounds
+constexpr int kMaxRegOpsPerPass = kTileOpSmemBytes / int(sizeof(RegOp));
+
+RegOp reg_op_from(const TileOp<float2> &t) {
+    RegOp r{};
+    for (int k = 0; k < 4; ++k) {
+        r.u[k] = t.u[k];
+        r.ul[k] = t.ul[k];
+    }
+    r.kind = t.kind;
+    r.lmask = t.lmask;
+    r.gmask = t.gmask;
+    r.gsel = t.gsel;
+    r.tb = (t.kind == K_PHASE1 || t.kind == K_DIAG) ? (1u << t.tl) : 0u;
+    return r;
+}
+
+// Group one pass's ops into rounds of RB slot qubits (greedy, moving an op
+// ahead only past ops it commutes with, as for the passes themselves).
+// Appends to regops / rounds; returns false if the pass cannot use them.
+bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_count, TilePassDesc &d, int RB,
+                  std::vector<RegOp> &regops, std::vector<RoundDesc> &rounds) {
+    struct Item {
+        RegOp op;
+        uint32_t N, A, tl;
+    };
+    const uint32_t all = (d.b >= 32) ? 0xffffffffu : ((1u << d.b) - 1);
+    std::vector<Item> items;
+    for (int i = op_begin; i < op_begin + op_count; ++i) {
+        const TileOp<float2> &t = ops[size_t(i)];
+        if (t.kind == K_DENSE && t.tab_off) {  // the phase table first, then the gate
+            Item it{};
+            it.op.kind = K_TAB;
+            it.op.gmask = 0;
+            it.op.tab_off = t.tab_off;
+            it.op.tw = uint8_t(t.tw + 1);
+            it.op.tpos[0] = uint8_t(t.tl);
+            for (int k = 0; k < t.tw; ++k) it.op.tpos[k + 1] = t.tpos[k];
+            it.op.tb = (t.tflags & 1) ? (1u << t.tl) : 0u;
+            uint32_t A = 1u << t.tl;
+            for (int k = 0; k < t.tw; ++k) A |= 1u << t.tpos[k];
+            it.N = 0;
+            it.A = A;
+            items.push_back(it);
+        }
+        Item it{};
+        it.op = reg_op_from(t);
+        it.tl = t.tl;
+        switch (t.kind) {
+            case K_DENSE:
+            case K_SWAPX:
+                it.N = 1u << t.tl;
+                it.A = it.N | t.lmask;
+                break;
+            case K_PHASE1:
+            case K_DIAG:
+                it.N = 0;
+                it.A = (1u << t.tl) | t.lmask;
+                break;
+            case K_SCALE:
+                it.N = 0;
+                it.A = t.lmask;
+                break;
+            default:  // K_PHRUN touches every qubit
+                it.N = 0;
+                it.A = all;
+                break;
+        }
+        items.push_back(it);
+    }
+    if (int(items.size()) > kMaxRegOpsPerPass) return false;
+    d.round_begin = int(rounds.size());
+    d.op_begin = int(regops.size());
+    std::vector<int> rem(items.size());
+    for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
+    bool first = true;
+    while (first || !rem.empty()) {
+        first = false;
+        uint32_t defN = 0, defA = 0, R = 0;
+        int nR = 0;
+        std::vector<int> take, keep;
+        for (int ii : rem) {
+            const Item &it = items[size_t(ii)];
+            bool ok = !((it.N & defA) || (it.A & defN));
+            if (ok && it.N && !(it.N & R)) {
+                if (nR < RB) {
+                    R |= it.N;
+                    ++nR;
+                } else {
+                    ok = false;
+                }
+            }
+            if (ok) {
+                take.push_back(ii);
+            } else {
+                keep.push_back(ii);
+                defN |= it.N;
+                defA |= it.A;
+            }
+        }
+        for (int q = d.b - 1; q >= 0 && nR < RB; --q)  // fill with the highest free tile qubits
+            if (!(R & (1u << q))) {
+                R |= 1u << q;
+                ++nR;
+            }
+        RoundDesc rd{};
+        int k = 0;
+        int slot_of[32];
+        for (int q = 0; q < 32; ++q) slot_of[q] = -1;
+        for (int q = 0; q < d.b; ++q)
+            if (R & (1u << q)) {
+                slot_of[q] = k;
+                rd.pos[k++] = uint8_t(q);
+            }
+        rd.op_begin = uint16_t(int(regops.size()) - d.op_begin);
+        rd.op_count = uint16_t(take.size());
+        for (int ii : take) {
+            RegOp op = items[size_t(ii)].op;
+            if (op.kind == K_DENSE || op.kind == K_SWAPX) op.k = uint8_t(slot_of[items[size_t(ii)].tl]);
+            if (op.kind == K_TAB) {
+                for (int c = 0; c < (1 << RB); ++c) {
+                    uint32_t e = 0;
+                    for (int j = 0; j < op.tw; ++j) {
+                        const int sl = slot_of[op.tpos[j]];
+                        if (sl >= 0 && ((c >> sl) & 1)) e |= 1u << j;
+                    }
+                    op.cidx[c] = uint8_t(e);
+                }
+            }
+            regops.push_back(op);
+        }
+        rounds.push_back(rd);
+        rem.swap(keep);
+    }
+    d.op_count = int(regops.size()) - d.op_begin;
+    d.round_count = int(rounds.size()) - d.round_begin;
+    return true;
 }
 
 // Greedy grouping of the gates into tile passes of at most 2^b amplitudes.
@@ -636,7 +779,10 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
     for (const Step &st : p->steps) {
         if (timed && !first)
             if (int rc = next_event(p, s)) return rc;
-        if (st.type == S_TILE) {
+        if (st.type == S_TILE && st.d.round_count > 0) {
+            if (int rc = launch_tile_reg(dst, first ? src : dst, p->M, st.d, p->d_regops, p->d_rounds, p->d_runs, s))
+                return rc;
+        } else if (st.type == S_TILE) {
             if (int rc = launch_tile_pass(dst, first ? src : dst, p->M, p->prec, st.d, p->d_ops, p->d_runs, s))
                 return rc;
         } else if (st.type == S_FUSED) {
@@ -735,12 +881,24 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
         const int b = o.tile_bits ? o.tile_bits : default_tile_bits(prec);
         p->tile_bits = std::min(b, M);
         int rc = tile_prepare(prec);
+        if (rc == QSIM_OK && prec == QSIM_C64) rc = tile_reg_prepare();
         std::vector<unsigned char> runs;
         if (rc == QSIM_OK) {
             if (prec == QSIM_C64) {
                 std::vector<TileOp<float2>> ops;
                 plan_tiled(p, b, ops, runs);
+                std::vector<RegOp> regops;
+                std::vector<RoundDesc> rounds;
+                for (Step &st : p->steps) {  // register rounds where the tile size allows
+                    if (st.type != S_TILE) continue;
+                    const int RB = st.d.b - kRegThreadBits;
+                    if (RB < 3 || RB > 4) continue;
+                    TilePassDesc d = st.d;
+                    if (build_rounds(ops, st.d.op_begin, st.d.op_count, d, RB, regops, rounds)) st.d = d;
+                }
                 rc = upload(p, &p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
+                if (rc == QSIM_OK) rc = upload(p, &p->d_regops, regops.data(), regops.size() * sizeof(RegOp), &p->regops_bytes);
+                if (rc == QSIM_OK) rc = upload(p, &p->d_rounds, rounds.data(), rounds.size() * sizeof(RoundDesc), &p->rounds_bytes);
             } else {
                 std::vector<TileOp<double2>> ops;
                 plan_tiled(p, b, ops, runs);
@@ -775,6 +933,8 @@ void plan_release(qsim_plan *p) {
     dev_free(p, p->d_ops);
     dev_free(p, p->d_runs);
     dev_free(p, p->d_rimg);
+    dev_free(p, p->d_regops);
+    dev_free(p, p->d_rounds);
     dev_free(p, p->d_status);
     delete p;
 }

@@ -38,7 +38,9 @@ int num_sms();  // streaming multiprocessors of the current device
 //   PHRUN  : (tile passes only) a run of diagonal gates with unit-modulus
 //            entries and at most one control, applied at once as a phase
 //            polynomial of the index bits (see PhaseRun).
-enum Kind : uint32_t { K_DENSE = 0, K_DIAG = 1, K_PHASE1 = 2, K_SWAPX = 3, K_SCALE = 4, K_PHRUN = 5 };
+//   TAB    : (register rounds) a run of phase gates inside the tile, one
+//            table lookup per amplitude.
+enum Kind : uint32_t { K_DENSE = 0, K_DIAG = 1, K_PHASE1 = 2, K_SWAPX = 3, K_SCALE = 4, K_PHRUN = 5, K_TAB = 6 };
 
 struct Gate {
     double U[8];
@@ -83,6 +85,7 @@ struct TilePassDesc {
     int hpos[kMaxTileHigh];
     int opos[QSIM_MAX_QUBITS];
     int op_begin, op_count;
+    int round_begin, round_count;  // register rounds (0 rounds: the shared-memory form)
 };
 
 template <typename T2>
@@ -126,6 +129,37 @@ using TurnT = typename std::conditional<sizeof(T2) == 8, uint32_t, uint64_t>::ty
 
 int launch_tile_pass(void *dst, const void *src, int M, qsim_prec prec, const TilePassDesc &d,
                      const void *ops_dev, const void *runs_dev, cudaStream_t s);
+
+// Register rounds (complex64 tile passes with b = kRegThreadBits + RB): each
+// of the block's 2^kRegThreadBits threads holds the 2^RB amplitudes of its
+// index that differ in RB chosen tile qubits (the round's slot qubits) in
+// registers and applies every gate of the round to them; shared memory is
+// touched only between rounds, and the first (last) round reads (writes)
+// device memory directly.
+constexpr int kRegThreadBits = 8;  // 256 threads
+struct RegOp {
+    float2 u[4], ul[4];  // matrix, hi and lo parts (dense and diagonal kinds)
+    uint32_t kind;       // K_DENSE, K_SWAPX, K_PHASE1, K_DIAG, K_SCALE, K_TAB, K_PHRUN
+    uint32_t lmask;      // controls inside the tile (tile-local bits)
+    uint64_t gmask;      // controls outside the tile
+    uint64_t gsel;       // K_SCALE: outside target bit; K_PHRUN: record offset in the run buffer
+    uint32_t tb;         // diagonal kinds: tile-local target bit; K_TAB: multiply only where this bit is set (0: all)
+    uint32_t tab_off;    // K_TAB: byte offset of the table in the run buffer
+    uint8_t k;           // pair kinds: slot bit of the target
+    uint8_t tw;          // K_TAB: index bits
+    uint8_t pad[2];
+    uint8_t tpos[12];    // K_TAB: tile-local positions of the index bits (bit j of the entry index)
+    uint8_t cidx[16];    // K_TAB: index contribution of slot c (the slot bits among tpos)
+};
+static_assert(sizeof(RegOp) % 16 == 0, "RegOp is copied in 16-byte units");
+struct RoundDesc {
+    uint8_t pos[4];        // slot qubits (tile-local positions), ascending
+    uint16_t op_begin;     // first op of the round, relative to the pass's first op
+    uint16_t op_count;
+};
+int launch_tile_reg(void *dst, const void *src, int M, const TilePassDesc &d, const void *ops_dev,
+                    const void *rounds_dev, const void *runs_dev, cudaStream_t s);
+int tile_reg_prepare();
 constexpr int kTileOpSmemBytes = 24 * 1024;  // a pass's ops are staged in shared memory up to this size
 int tile_max_bits(qsim_prec prec);
 int tile_prepare(qsim_prec prec);  // one-time kernel attributes (call before any stream capture)
