@@ -28,20 +28,32 @@ struct Slots {
     float2 x[S];
 };
 
-// Pair update on slot bit K: pairs (c, c | 2^K) of this thread's slots.
-template <int RB, int K, bool SWAP>
-__device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op, uint32_t i0, const uint32_t *dep) {
+// Shared-memory position of tile index i: the low 4 bits are XORed with the
+// next 4, so that the 32 lanes of a warp fall on different banks also when a
+// round's slot qubits are the tile's lowest.
+__device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ ((i >> 4) & 0xFu); }
+
+// Pair update on slot bit K: pairs (c, c | 2^K) of this thread's slots, for
+// the lower slots c in op.smask (controls on slot qubits are folded into the
+// mask, controls on other tile qubits into op.nmask, tested by the caller).
+template <int RB, int K, bool SWAP, bool REAL>
+__device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op) {
     constexpr int S = 1 << RB;
+    const uint32_t sm = op.smask;
 #pragma unroll
     for (int c = 0; c < S; ++c) {
         if (c & (1 << K)) continue;
+        if (!((sm >> c) & 1u)) continue;
         const int c1 = c | (1 << K);
-        const uint32_t i = i0 | dep[c];
-        if ((i & op.lmask) != op.lmask) continue;
         const float2 a = v.x[c], b = v.x[c1];
         if (SWAP) {
             v.x[c] = b;
             v.x[c1] = a;
+        } else if (REAL) {  // real entries: (u + ul) a + (w + wl) b per component
+            v.x[c] = make_float2(fmaf(op.u[0].x, a.x, fmaf(op.u[1].x, b.x, fmaf(op.ul[0].x, a.x, op.ul[1].x * b.x))),
+                                 fmaf(op.u[0].x, a.y, fmaf(op.u[1].x, b.y, fmaf(op.ul[0].x, a.y, op.ul[1].x * b.y))));
+            v.x[c1] = make_float2(fmaf(op.u[2].x, a.x, fmaf(op.u[3].x, b.x, fmaf(op.ul[2].x, a.x, op.ul[3].x * b.x))),
+                                  fmaf(op.u[2].x, a.y, fmaf(op.u[3].x, b.y, fmaf(op.ul[2].x, a.y, op.ul[3].x * b.y))));
         } else {
             v.x[c] = cmad2x(op.u[0], op.ul[0], a, op.u[1], op.ul[1], b);
             v.x[c1] = cmad2x(op.u[2], op.ul[2], a, op.u[3], op.ul[3], b);
@@ -49,37 +61,56 @@ __device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op, uint32_t i0
     }
 }
 
-template <int RB, bool SWAP>
-__device__ __forceinline__ void pairs_any(Slots<RB> &v, const RegOp &op, uint32_t i0, const uint32_t *dep) {
+template <int RB, bool SWAP, bool REAL>
+__device__ __forceinline__ void pairs_any(Slots<RB> &v, const RegOp &op) {
     switch (op.k) {
-        case 0: pairs<RB, 0, SWAP>(v, op, i0, dep); break;
-        case 1: pairs<RB, 1, SWAP>(v, op, i0, dep); break;
-        case 2: pairs<RB, 2, SWAP>(v, op, i0, dep); break;
-        default: if constexpr (RB > 3) pairs<RB, 3, SWAP>(v, op, i0, dep); break;
+        case 0: pairs<RB, 0, SWAP, REAL>(v, op); break;
+        case 1: pairs<RB, 1, SWAP, REAL>(v, op); break;
+        case 2: pairs<RB, 2, SWAP, REAL>(v, op); break;
+        default: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL>(v, op); break;
     }
 }
 
 template <int RB>
-__device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t i0, const uint32_t *dep,
+__device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t i0, const RoundDesc &R,
                                          uint64_t base, uint64_t tile, const TilePassDesc &d,
                                          const unsigned char *__restrict__ runs, RunSmem<uint32_t> &rs) {
     constexpr int S = 1 << RB;
+    if (op.kind == K_PHRUN) {  // every thread reaches the synchronisations inside
+        const uint32_t *Q = phase_run_setup<uint32_t>(d, tile, runs + op.gsel, rs);
+        const int bl = d.b < 7 ? d.b : 7;
+        const uint32_t lomask = (1u << bl) - 1;
+        const uint32_t kt = rs.kt;
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            uint32_t i = i0;
+#pragma unroll
+            for (int k = 0; k < RB; ++k)
+                if (c & (1 << k)) i |= 1u << R.pos[k];
+            const uint32_t phi = kt + rs.lin_lo[i & lomask] + rs.lin_hi[i >> bl] + __ldg(Q + i);
+            v.x[c] = cmul(expi_turns(phi), v.x[c]);
+        }
+        return;
+    }
+    if ((i0 & op.nmask) != op.nmask) return;  // a control (or the target) outside the slots is 0
+    const uint32_t sm = op.smask;
     switch (op.kind) {
-        case K_DENSE: pairs_any<RB, false>(v, op, i0, dep); break;
-        case K_SWAPX: pairs_any<RB, true>(v, op, i0, dep); break;
+        case K_DENSE: pairs_any<RB, false, false>(v, op); break;
+        case K_RDENSE: pairs_any<RB, false, true>(v, op); break;
+        case K_SWAPX: pairs_any<RB, true, false>(v, op); break;
         case K_PHASE1: {
-            const uint32_t m = op.lmask | op.tb;
 #pragma unroll
             for (int c = 0; c < S; ++c)
-                if (((i0 | dep[c]) & m) == m) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
+                if ((sm >> c) & 1u) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
             break;
         }
         case K_DIAG: {
+            const bool up_thread = (i0 & op.tbn) != 0;
 #pragma unroll
             for (int c = 0; c < S; ++c) {
-                const uint32_t i = i0 | dep[c];
-                if ((i & op.lmask) != op.lmask) continue;
-                v.x[c] = (i & op.tb) ? cmulx(op.u[3], op.ul[3], v.x[c]) : cmulx(op.u[0], op.ul[0], v.x[c]);
+                if (!((sm >> c) & 1u)) continue;
+                const bool up = op.tbn ? up_thread : ((op.tsel >> c) & 1u);
+                v.x[c] = up ? cmulx(op.u[3], op.ul[3], v.x[c]) : cmulx(op.u[0], op.ul[0], v.x[c]);
             }
             break;
         }
@@ -88,7 +119,7 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
             const float2 f = up ? op.u[3] : op.u[0], fl = up ? op.ul[3] : op.ul[0];
 #pragma unroll
             for (int c = 0; c < S; ++c)
-                if (((i0 | dep[c]) & op.lmask) == op.lmask) v.x[c] = cmulx(f, fl, v.x[c]);
+                if ((sm >> c) & 1u) v.x[c] = cmulx(f, fl, v.x[c]);
             break;
         }
         case K_TAB: {
@@ -97,22 +128,9 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
             const float4 *tab = reinterpret_cast<const float4 *>(runs + op.tab_off);
 #pragma unroll
             for (int c = 0; c < S; ++c) {
-                if (op.tb && !((i0 | dep[c]) & op.tb)) continue;
+                if (!((sm >> c) & 1u)) continue;
                 const float4 t = __ldg(tab + (g | op.cidx[c]));
                 v.x[c] = cmulx(make_float2(t.x, t.y), make_float2(t.z, t.w), v.x[c]);
-            }
-            break;
-        }
-        case K_PHRUN: {
-            const uint32_t *Q = phase_run_setup<uint32_t>(d, tile, runs + op.gsel, rs);
-            const int bl = d.b < 7 ? d.b : 7;
-            const uint32_t lomask = (1u << bl) - 1;
-            const uint32_t kt = rs.kt;
-#pragma unroll
-            for (int c = 0; c < S; ++c) {
-                const uint32_t i = i0 | dep[c];
-                const uint32_t phi = kt + rs.lin_lo[i & lomask] + rs.lin_hi[i >> bl] + __ldg(Q + i);
-                v.x[c] = cmul(expi_turns(phi), v.x[c]);
             }
             break;
         }
@@ -176,12 +194,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_reg(float2 *dst, const flo
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < S; ++c) v.x[c] = s[i0 | dep[c]];
+                for (int c = 0; c < S; ++c) v.x[c] = s[swz(i0 | dep[c])];
             }
             for (int k = R.op_begin; k < R.op_begin + R.op_count; ++k) {
                 const RegOp &op = sops[k];
                 if ((base & op.gmask) != op.gmask) continue;  // uniform over the block
-                apply_op<RB>(v, op, i0, dep, base, tile, d, runs, rs);
+                apply_op<RB>(v, op, i0, R, base, tile, d, runs, rs);
             }
             if (rd + 1 == d.round_count) {
 #pragma unroll
@@ -192,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_reg(float2 *dst, const flo
             } else {
                 __syncthreads();  // every thread has read its amplitudes of the previous round
 #pragma unroll
-                for (int c = 0; c < S; ++c) s[i0 | dep[c]] = v.x[c];
+                for (int c = 0; c < S; ++c) s[swz(i0 | dep[c])] = v.x[c];
                 __syncthreads();
             }
         }

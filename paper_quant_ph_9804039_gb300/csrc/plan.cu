@@ -299,6 +299,11 @@ RegOp reg_op_from(const TileOp<float2> &t) {
     r.gmask = t.gmask;
     r.gsel = t.gsel;
     r.tb = (t.kind == K_PHASE1 || t.kind == K_DIAG) ? (1u << t.tl) : 0u;
+    if (t.kind == K_DENSE) {
+        bool real = true;
+        for (int k = 0; k < 4; ++k) real = real && t.u[k].y == 0.f && t.ul[k].y == 0.f;
+        if (real) r.kind = K_RDENSE;
+    }
     return r;
 }
 
@@ -336,6 +341,7 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
         switch (t.kind) {
             case K_DENSE:
             case K_SWAPX:
+            case K_RDENSE:
                 it.N = 1u << t.tl;
                 it.A = it.N | t.lmask;
                 break;
@@ -401,9 +407,56 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
             }
         rd.op_begin = uint16_t(int(regops.size()) - d.op_begin);
         rd.op_count = uint16_t(take.size());
+        const uint32_t Rmask = R;
+        // slots c whose slot-qubit bits include all of m's slot bits
+        auto slot_mask = [&](uint32_t m, int skip_bit) {
+            uint32_t sm = 0;
+            for (int c = 0; c < (1 << RB); ++c) {
+                if (skip_bit >= 0 && ((c >> skip_bit) & 1)) continue;
+                bool ok = true;
+                for (int q = 0; q < 32; ++q)
+                    if ((m & Rmask & (1u << q)) && !((c >> slot_of[q]) & 1)) ok = false;
+                if (ok) sm |= 1u << c;
+            }
+            return uint16_t(sm);
+        };
         for (int ii : take) {
             RegOp op = items[size_t(ii)].op;
-            if (op.kind == K_DENSE || op.kind == K_SWAPX) op.k = uint8_t(slot_of[items[size_t(ii)].tl]);
+            const uint32_t tbit = 1u << items[size_t(ii)].tl;
+            switch (op.kind) {
+                case K_DENSE:
+                case K_SWAPX:
+                case K_RDENSE:
+                    op.k = uint8_t(slot_of[items[size_t(ii)].tl]);
+                    op.smask = slot_mask(op.lmask, op.k);
+                    op.nmask = op.lmask & ~Rmask;
+                    break;
+                case K_PHASE1:
+                    op.smask = slot_mask(op.lmask | tbit, -1);
+                    op.nmask = (op.lmask | tbit) & ~Rmask;
+                    break;
+                case K_DIAG:
+                    op.smask = slot_mask(op.lmask, -1);
+                    op.nmask = op.lmask & ~Rmask;
+                    if (Rmask & tbit) {
+                        op.tbn = 0;
+                        for (int c = 0; c < (1 << RB); ++c)
+                            if ((c >> slot_of[items[size_t(ii)].tl]) & 1) op.tsel |= uint16_t(1u << c);
+                    } else {
+                        op.tbn = tbit;
+                    }
+                    break;
+                case K_SCALE:
+                    op.smask = slot_mask(op.lmask, -1);
+                    op.nmask = op.lmask & ~Rmask;
+                    break;
+                case K_TAB:
+                    op.smask = slot_mask(op.tb, -1);
+                    op.nmask = op.tb & ~Rmask;
+                    break;
+                default:
+                    break;
+            }
             if (op.kind == K_TAB) {
                 for (int c = 0; c < (1 << RB); ++c) {
                     uint32_t e = 0;
@@ -422,6 +475,60 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
     d.op_count = int(regops.size()) - d.op_begin;
     d.round_count = int(rounds.size()) - d.round_begin;
     return true;
+}
+
+// An uncontrolled dense gate whose rows are real up to one phase each,
+// U = diag(e^{ia}, e^{ib}) O with O real (a noisy Hadamard, a NOT with a
+// phase error), becomes the real gate O followed by the diagonal phase gate;
+// the pass scheduler then moves the phase gate into the next run of phase
+// gates, and O costs half the arithmetic of a complex 2x2.
+void split_row_phases(std::vector<Gate> &gates) {
+    std::vector<Gate> out;
+    out.reserve(gates.size() * 2);
+    for (const Gate &g : gates) {
+        if (g.kind != K_DENSE || g.nc != 0) {
+            out.push_back(g);
+            continue;
+        }
+        double ph[2];
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; ++r) {
+            const double *e0 = g.U + 4 * r, *e1 = g.U + 4 * r + 2;  // row r: (re, im) of both entries
+            const double m0 = std::hypot(e0[0], e0[1]), m1 = std::hypot(e1[0], e1[1]);
+            const double *big = m0 >= m1 ? e0 : e1;
+            ph[r] = std::atan2(big[1], big[0]);
+            // the other entry must have the same phase (or be zero): Im(e conj(big)) = 0
+            const double *other = m0 >= m1 ? e1 : e0;
+            const double cross = other[1] * big[0] - other[0] * big[1];
+            ok = std::fabs(cross) <= 1e-14 * (m0 * m0 + m1 * m1);
+        }
+        if (!ok) {
+            out.push_back(g);
+            continue;
+        }
+        Gate o = g, dg = g;
+        for (int r = 0; r < 2; ++r) {
+            const double c = std::cos(ph[r]), sn = std::sin(ph[r]);
+            for (int e = 0; e < 2; ++e) {  // O = e^{-i ph_r} row r, real
+                const double re = g.U[4 * r + 2 * e], im = g.U[4 * r + 2 * e + 1];
+                o.U[4 * r + 2 * e] = re * c + im * sn;
+                o.U[4 * r + 2 * e + 1] = 0.0;
+            }
+        }
+        for (int k = 0; k < 8; ++k) dg.U[k] = 0.0;
+        dg.U[0] = ph[0] == 0.0 ? 1.0 : std::cos(ph[0]);
+        dg.U[1] = ph[0] == 0.0 ? 0.0 : std::sin(ph[0]);
+        dg.U[6] = std::cos(ph[1]);
+        dg.U[7] = std::sin(ph[1]);
+        dg.kind = (dg.U[0] == 1.0 && dg.U[1] == 0.0) ? K_PHASE1 : K_DIAG;
+        if (ph[0] == 0.0 && ph[1] == 0.0) {
+            out.push_back(o);  // already real
+        } else {
+            out.push_back(o);
+            out.push_back(dg);
+        }
+    }
+    gates.swap(out);
 }
 
 // Greedy grouping of the gates into tile passes of at most 2^b amplitudes.
@@ -882,6 +989,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
         p->tile_bits = std::min(b, M);
         int rc = tile_prepare(prec);
         if (rc == QSIM_OK && prec == QSIM_C64) rc = tile_reg_prepare();
+        if (prec == QSIM_C64) split_row_phases(p->gates);
         std::vector<unsigned char> runs;
         if (rc == QSIM_OK) {
             if (prec == QSIM_C64) {

@@ -40,7 +40,10 @@ int num_sms();  // streaming multiprocessors of the current device
 //            polynomial of the index bits (see PhaseRun).
 //   TAB    : (register rounds) a run of phase gates inside the tile, one
 //            table lookup per amplitude.
-enum Kind : uint32_t { K_DENSE = 0, K_DIAG = 1, K_PHASE1 = 2, K_SWAPX = 3, K_SCALE = 4, K_PHRUN = 5, K_TAB = 6 };
+//   RDENSE : (register rounds) a dense gate with real entries.
+enum Kind : uint32_t {
+    K_DENSE = 0, K_DIAG = 1, K_PHASE1 = 2, K_SWAPX = 3, K_SCALE = 4, K_PHRUN = 5, K_TAB = 6, K_RDENSE = 7
+};
 
 struct Gate {
     double U[8];
@@ -147,9 +150,13 @@ struct RegOp {
     uint32_t tab_off;    // K_TAB: byte offset of the table in the run buffer
     uint8_t k;           // pair kinds: slot bit of the target
     uint8_t tw;          // K_TAB: index bits
-    uint8_t pad[2];
+    uint16_t smask;      // slots the op touches (pair kinds: the lower slot of each pair)
     uint8_t tpos[12];    // K_TAB: tile-local positions of the index bits (bit j of the entry index)
     uint8_t cidx[16];    // K_TAB: index contribution of slot c (the slot bits among tpos)
+    uint32_t nmask;      // tile bits outside the slots that the thread's index must have set
+    uint32_t tbn;        // K_DIAG: target bit when it is not a slot qubit (tested on the thread's index)
+    uint16_t tsel;       // K_DIAG: slots whose target bit is set (target a slot qubit)
+    uint16_t pad2[3];
 };
 static_assert(sizeof(RegOp) % 16 == 0, "RegOp is copied in 16-byte units");
 struct RoundDesc {

@@ -50,22 +50,24 @@ __device__ const Turn *phase_run_setup(const TilePassDesc &d, uint64_t tile, con
     const int b = d.b;
     const int t = threadIdx.x;
     __syncthreads();  // rs may still be read by a previous run
-    if (t < b) {
+    if (t < b) {  // warp 0: linear coefficient of each tile-local bit, given the tile's outside bits
         const int q = t < d.L ? t : d.hpos[t - d.L];
         Turn v = c[q];
         for (int k = 0; k < d.nout; ++k)
             if ((tile >> k) & 1) v += w[q * M + d.opos[k]];
         rs.cl[t] = v;
-    } else if (t == 32) {
-        Turn v = *c0p;
-        for (int k = 0; k < d.nout; ++k) {
+    } else if (t >= 32 && t < 64) {  // warp 1: the tile's constant, one outside bit per lane
+        Turn v = 0;
+        for (int k = t - 32; k < d.nout; k += 32) {
             if (!((tile >> k) & 1)) continue;
             const int r = d.opos[k];
             v += c[r];
             for (int k2 = k + 1; k2 < d.nout; ++k2)
                 if ((tile >> k2) & 1) v += w[r * M + d.opos[k2]];
         }
-        rs.kt = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (t == 32) rs.kt = v + *c0p;
     }
     __syncthreads();
     const int bl = b < 7 ? b : 7;
