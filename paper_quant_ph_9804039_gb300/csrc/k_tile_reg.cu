@@ -21,6 +21,7 @@ namespace qs {
 namespace {
 
 constexpr int kThreads = 1 << kRegThreadBits;
+constexpr int kThreadsPerBlock = kThreads;
 
 template <int RB>
 struct Slots {
@@ -33,17 +34,58 @@ struct Slots {
 // round's slot qubits are the tile's lowest.
 __device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ ((i >> 4) & 0xFu); }
 
+// Per-tile state of a phase-polynomial record (K_PHRUN), double-buffered:
+// consecutive records of a block alternate between the two copies, so the
+// one barrier inside each set-up also orders the writes of a record against
+// the reads of the record two before it.
+struct PhRunState {
+    uint32_t cl[2][16];  // linear coefficient of each tile-local bit, given the tile's outside bits
+    uint32_t ktw[2][8];  // the tile's constant, one partial sum per warp
+};
+
+// Phi(i) = c0 + sum_q c_q i_q + sum_{q<r} w_qr i_q i_r (turns of 2^-32) on
+// the tile with outside bits `tile`: tile-local bit t gets
+// cl[t] = c_{q_t} + sum over set outside bits k of w[q_t][r_k] (warp t mod 8,
+// one outside bit per lane, summed with a warp reduction), and the constant
+// sums c_{r_k} + w[r_k][r_k2] over set outside bits k <= k2 (all threads, one
+// (k, k2) pair each).  All threads of the block call it.
+__device__ __forceinline__ void phrun_setup(const TilePassDesc &d, uint64_t tile, const unsigned char *__restrict__ rec,
+                                            PhRunState &ps, int buf) {
+    const PhaseRunHdr h = *reinterpret_cast<const PhaseRunHdr *>(rec);
+    const int M = int(h.M);
+    const uint32_t *c = reinterpret_cast<const uint32_t *>(rec + sizeof(PhaseRunHdr)) + 1;
+    const uint32_t *w = c + M;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nout = d.nout;
+    const bool set = lane < nout && ((tile >> lane) & 1);
+    const int r = lane < nout ? d.opos[lane] : 0;
+    for (int t = warp; t < d.b; t += kThreadsPerBlock / 32) {
+        const int q = t < d.L ? t : d.hpos[t - d.L];
+        const uint32_t v = __reduce_add_sync(0xffffffffu, set ? __ldg(w + q * M + r) : 0u);
+        if (lane == 0) ps.cl[buf][t] = v + __ldg(c + q);
+    }
+    uint32_t kv = 0;
+    for (int p = threadIdx.x; p < nout * nout; p += kThreadsPerBlock) {
+        const int k = p / nout, k2 = p - k * nout;
+        if (k2 < k || !((tile >> k) & 1) || !((tile >> k2) & 1)) continue;
+        kv += k2 == k ? __ldg(c + d.opos[k]) : __ldg(w + d.opos[k] * M + d.opos[k2]);
+    }
+    kv = __reduce_add_sync(0xffffffffu, kv);
+    if (lane == 0) ps.ktw[buf][warp] = kv;
+    __syncthreads();
+}
+
 // Pair update on slot bit K: pairs (c, c | 2^K) of this thread's slots, for
 // the lower slots c in op.smask (controls on slot qubits are folded into the
 // mask, controls on other tile qubits into op.nmask, tested by the caller).
-template <int RB, int K, bool SWAP, bool REAL>
+template <int RB, int K, bool SWAP, bool REAL, bool ALL>
 __device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op) {
     constexpr int S = 1 << RB;
     const uint32_t sm = op.smask;
 #pragma unroll
     for (int c = 0; c < S; ++c) {
         if (c & (1 << K)) continue;
-        if (!((sm >> c) & 1u)) continue;
+        if (!ALL && !((sm >> c) & 1u)) continue;
         const int c1 = c | (1 << K);
         const float2 a = v.x[c], b = v.x[c1];
         if (SWAP) {
@@ -61,35 +103,62 @@ __device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op) {
     }
 }
 
+template <int RB, bool SWAP, bool REAL, bool ALL>
+__device__ __forceinline__ void pairs_k(Slots<RB> &v, const RegOp &op) {
+    switch (op.k) {
+        case 0: pairs<RB, 0, SWAP, REAL, ALL>(v, op); break;
+        case 1: pairs<RB, 1, SWAP, REAL, ALL>(v, op); break;
+        case 2: pairs<RB, 2, SWAP, REAL, ALL>(v, op); break;
+        default: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL, ALL>(v, op); break;
+    }
+}
+
+// op.smask covering every pair (no control among the slot qubits) takes the
+// unconditional form.
 template <int RB, bool SWAP, bool REAL>
 __device__ __forceinline__ void pairs_any(Slots<RB> &v, const RegOp &op) {
-    switch (op.k) {
-        case 0: pairs<RB, 0, SWAP, REAL>(v, op); break;
-        case 1: pairs<RB, 1, SWAP, REAL>(v, op); break;
-        case 2: pairs<RB, 2, SWAP, REAL>(v, op); break;
-        default: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL>(v, op); break;
-    }
+    uint32_t want = 0;  // lower slots of all pairs on slot bit k
+#pragma unroll
+    for (int c = 0; c < (1 << RB); ++c)
+        if (!((c >> op.k) & 1)) want |= 1u << c;
+    if (op.smask == want)
+        pairs_k<RB, SWAP, REAL, true>(v, op);
+    else
+        pairs_k<RB, SWAP, REAL, false>(v, op);
 }
 
 template <int RB>
 __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t i0, const RoundDesc &R,
                                          uint64_t base, uint64_t tile, const TilePassDesc &d,
-                                         const unsigned char *__restrict__ runs, RunSmem<uint32_t> &rs) {
+                                         const unsigned char *__restrict__ runs, PhRunState &ps, int &nrun) {
     constexpr int S = 1 << RB;
-    if (op.kind == K_PHRUN) {  // every thread reaches the synchronisations inside
-        const uint32_t *Q = phase_run_setup<uint32_t>(d, tile, runs + op.gsel, rs);
-        const int bl = d.b < 7 ? d.b : 7;
-        const uint32_t lomask = (1u << bl) - 1;
-        const uint32_t kt = rs.kt;
+    if (op.kind == K_PHRUN) {  // every thread reaches the synchronisation inside
+        // Phi(i0 | slots c) = Phi(i0) + sum_{k in c} (cl[pos_k] + Q(i0 | bit_k) - Q(i0)) + Q(slots c):
+        // five exponentials per thread, the slot-only factors e^{i Q(slots c)} precomputed.
+        const unsigned char *rec = runs + op.gsel;
+        const int buf = nrun++ & 1;
+        phrun_setup(d, tile, rec, ps, buf);
+        const PhaseRunHdr h = *reinterpret_cast<const PhaseRunHdr *>(rec);
+        const uint32_t *Q = reinterpret_cast<const uint32_t *>(rec + h.q_offset);
+        const uint32_t q0 = __ldg(Q + i0);
+        uint32_t phi = __ldg(reinterpret_cast<const uint32_t *>(rec + sizeof(PhaseRunHdr))) + q0;
 #pragma unroll
-        for (int c = 0; c < S; ++c) {
-            uint32_t i = i0;
+        for (int j = 0; j < kThreadsPerBlock / 32; ++j) phi += ps.ktw[buf][j];
 #pragma unroll
-            for (int k = 0; k < RB; ++k)
-                if (c & (1 << k)) i |= 1u << R.pos[k];
-            const uint32_t phi = kt + rs.lin_lo[i & lomask] + rs.lin_hi[i >> bl] + __ldg(Q + i);
-            v.x[c] = cmul(expi_turns(phi), v.x[c]);
+        for (int t = 0; t < 16; ++t)
+            if ((i0 >> t) & 1) phi += ps.cl[buf][t];
+        float2 e[S];
+        e[0] = expi_turns(phi);
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            const uint32_t pk = R.pos[k];
+            const float2 dk = expi_turns(ps.cl[buf][pk] + __ldg(Q + (i0 | (1u << pk))) - q0);
+#pragma unroll
+            for (int c = 0; c < (1 << k); ++c) e[c | (1 << k)] = cmul(e[c], dk);
         }
+        const float2 *f = reinterpret_cast<const float2 *>(runs + op.tab_off);
+#pragma unroll
+        for (int c = 0; c < S; ++c) v.x[c] = cmul(cmul(e[c], __ldg(f + c)), v.x[c]);
         return;
     }
     if ((i0 & op.nmask) != op.nmask) return;  // a control (or the target) outside the slots is 0
@@ -99,9 +168,14 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
         case K_RDENSE: pairs_any<RB, false, true>(v, op); break;
         case K_SWAPX: pairs_any<RB, true, false>(v, op); break;
         case K_PHASE1: {
+            if (sm == (1u << S) - 1) {
 #pragma unroll
-            for (int c = 0; c < S; ++c)
-                if ((sm >> c) & 1u) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
+                for (int c = 0; c < S; ++c) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < S; ++c)
+                    if ((sm >> c) & 1u) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
+            }
             break;
         }
         case K_DIAG: {
@@ -139,7 +213,7 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
 }
 
 template <int RB>
-__global__ void __launch_bounds__(kThreads, 2) k_tile_reg(float2 *dst, const float2 *src, TilePassDesc d,
+__global__ void __launch_bounds__(kThreads, 3) k_tile_reg(float2 *dst, const float2 *src, TilePassDesc d,
                                                           const RegOp *__restrict__ ops,
                                                           const RoundDesc *__restrict__ rounds,
                                                           const unsigned char *__restrict__ runs, uint64_t ntiles) {
@@ -148,7 +222,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_reg(float2 *dst, const flo
     float2 *s = reinterpret_cast<float2 *>(smem_raw);
     RegOp *sops = reinterpret_cast<RegOp *>(smem_raw + (d.round_count > 1 ? (size_t(1) << d.b) * sizeof(float2) : 0));
     __shared__ uint64_t hoff[1 << kMaxTileHigh];
-    __shared__ RunSmem<uint32_t> rs;
+    __shared__ PhRunState ps;
+    int nrun = 0;  // K_PHRUN records met so far (uniform over the block)
     const int tid = threadIdx.x;
     {  // the pass's ops, staged once
         const int4 *g4 = reinterpret_cast<const int4 *>(ops + d.op_begin);
@@ -199,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_reg(float2 *dst, const flo
             for (int k = R.op_begin; k < R.op_begin + R.op_count; ++k) {
                 const RegOp &op = sops[k];
                 if ((base & op.gmask) != op.gmask) continue;  // uniform over the block
-                apply_op<RB>(v, op, i0, R, base, tile, d, runs, rs);
+                apply_op<RB>(v, op, i0, R, base, tile, d, runs, ps, nrun);
             }
             if (rd + 1 == d.round_count) {
 #pragma unroll
@@ -240,10 +315,11 @@ int launch_tile_reg(void *dst, const void *src, int M, const TilePassDesc &d, co
     if (int rc = tile_reg_prepare()) return rc;
     const uint64_t ntiles = uint64_t(1) << (M - d.b);
     const size_t smem = (d.round_count > 1 ? (size_t(1) << d.b) * sizeof(float2) : 0) + size_t(d.op_count) * sizeof(RegOp);
-    int per_sm = int((220 * 1024) / (smem + 6144));
+    int per_sm = 0;
+    if (RB == 3) QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_reg<3>, kThreads, smem));
+    else QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_reg<4>, kThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 2048 / kThreads) per_sm = 2048 / kThreads;
-    uint64_t grid = uint64_t(num_sms()) * per_sm;
+    uint64_t grid = uint64_t(num_sms()) * per_sm;  // one wave of resident blocks, each looping over tiles
     if (grid > ntiles) grid = ntiles;
     const RegOp *ops = static_cast<const RegOp *>(ops_dev);
     const RoundDesc *rounds = static_cast<const RoundDesc *>(rounds_dev);

@@ -17,7 +17,7 @@
 
 namespace qs {
 
-enum StepType { S_GATE = 0, S_TILE = 1, S_FUSED = 2 };
+enum StepType { S_GATE = 0, S_TILE = 1, S_FUSED = 2, S_PERM = 3 };
 
 struct Step {
     StepType type;
@@ -25,6 +25,7 @@ struct Step {
     TilePassDesc d;  // S_TILE
     FusedDesc f;     // S_FUSED
     size_t rimg;     // S_FUSED: float offset of the block's R image
+    PermDesc perm;   // S_PERM
     double bytes;
 };
 
@@ -311,7 +312,7 @@ RegOp reg_op_from(const TileOp<float2> &t) {
 // ahead only past ops it commutes with, as for the passes themselves).
 // Appends to regops / rounds; returns false if the pass cannot use them.
 bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_count, TilePassDesc &d, int RB,
-                  std::vector<RegOp> &regops, std::vector<RoundDesc> &rounds) {
+                  std::vector<RegOp> &regops, std::vector<RoundDesc> &rounds, std::vector<unsigned char> &runs) {
     struct Item {
         RegOp op;
         uint32_t N, A, tl;
@@ -457,6 +458,23 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
                 default:
                     break;
             }
+            if (op.kind == K_PHRUN) {  // e^{i Q(slots c)} of this round, for every slot c
+                PhaseRunHdr h;
+                std::memcpy(&h, runs.data() + op.gsel, sizeof h);
+                const uint32_t *Q = reinterpret_cast<const uint32_t *>(runs.data() + op.gsel + h.q_offset);
+                float2 f[16];
+                for (int c = 0; c < (1 << RB); ++c) {
+                    uint32_t dep = 0;
+                    for (int k2 = 0; k2 < RB; ++k2)
+                        if ((c >> k2) & 1) dep |= 1u << rd.pos[k2];
+                    const double ang = 2.0 * M_PI * double(Q[dep]) / 4294967296.0;
+                    f[c] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+                }
+                const size_t start = (runs.size() + 15) & ~size_t(15);
+                runs.resize(start + sizeof(f), 0);
+                std::memcpy(runs.data() + start, f, sizeof(f));
+                op.tab_off = uint32_t(start);
+            }
             if (op.kind == K_TAB) {
                 for (int c = 0; c < (1 << RB); ++c) {
                     uint32_t e = 0;
@@ -531,15 +549,85 @@ void split_row_phases(std::vector<Gate> &gates) {
     gates.swap(out);
 }
 
+// Runs of SWAP gates written as three exact CNOTs (a->b, b->a, a->b).
+// Returns, for every gate, -1 or the id of the run it belongs to, and the
+// runs' qubit permutations (pi[q] = new position of qubit q).
+int find_swap_runs(const std::vector<Gate> &g, std::vector<int> &run_of, std::vector<std::vector<int>> &perms, int M) {
+    run_of.assign(g.size(), -1);
+    int nrun = 0;
+    size_t i = 0;
+    while (i + 2 < g.size()) {
+        auto is_swap = [&](size_t k) {
+            const Gate &a = g[k], &b = g[k + 1], &c = g[k + 2];
+            return a.kind == K_SWAPX && b.kind == K_SWAPX && c.kind == K_SWAPX && a.nc == 1 && b.nc == 1 &&
+                   c.nc == 1 && a.t == c.t && a.c[0] == c.c[0] && b.t == a.c[0] && b.c[0] == a.t;
+        };
+        if (!is_swap(i)) {
+            ++i;
+            continue;
+        }
+        std::vector<int> pi(M);
+        for (int q = 0; q < M; ++q) pi[q] = q;
+        size_t j = i;
+        while (j + 2 < g.size() && is_swap(j)) {
+            const int a = g[j].c[0], b = g[j].t;
+            for (int q = 0; q < M; ++q) {  // compose: positions a and b exchange
+                if (pi[q] == a) pi[q] = b;
+                else if (pi[q] == b) pi[q] = a;
+            }
+            for (size_t k = j; k < j + 3; ++k) run_of[k] = nrun;
+            j += 3;
+        }
+        bool invol = true;
+        for (int q = 0; q < M; ++q) invol = invol && pi[pi[q]] == q;
+        if (!invol) {  // leave it as gates
+            for (size_t k = i; k < j; ++k) run_of[k] = -1;
+        } else {
+            perms.push_back(pi);
+            ++nrun;
+        }
+        i = j;
+    }
+    return nrun;
+}
+
+// Tile of the permutation pass: the lowest lb qubits (contiguous runs of
+// 2^lb amplitudes) and their images under pi, with lb as large as the shared
+// memory of two tiles allows (at most 12 tile qubits).
+PermDesc perm_desc(const std::vector<int> &pi, int M, qsim_prec prec) {
+    PermDesc best{};
+    for (int lb = std::min(6, M); lb >= 1; --lb) {
+        PermDesc d{};
+        d.lb = lb;
+        uint64_t S = 0;
+        for (int q = 0; q < lb; ++q) S |= bit(q) | bit(pi[q]);
+        if (__builtin_popcountll(S) > 12) continue;
+        int sidx[64], oidx[64];
+        for (int q = 0; q < M; ++q) {
+            if (S & bit(q)) {
+                sidx[q] = d.ns;
+                d.spos[d.ns++] = q;
+            } else {
+                oidx[q] = d.nout;
+                d.opos[d.nout++] = q;
+            }
+        }
+        for (int j = 0; j < d.ns; ++j) d.spi[j] = sidx[pi[d.spos[j]]];
+        for (int j = 0; j < d.nout; ++j) d.opi[j] = oidx[pi[d.opos[j]]];
+        if (perm_smem_bytes(d, prec) <= 96 * 1024) return d;
+        best = d;
+    }
+    return best;
+}
+
 // Greedy grouping of the gates into tile passes of at most 2^b amplitudes.
 template <typename T2>
-void plan_tiled(qsim_plan *p, int b_req, std::vector<TileOp<T2>> &ops, std::vector<unsigned char> &runs) {
+void plan_tiled(qsim_plan *p, int b_req, std::vector<int> rem, std::vector<TileOp<T2>> &ops,
+                std::vector<unsigned char> &runs) {
     const int M = p->M;
     const int b = std::min(b_req, M);
     const int L = std::min(b, p->prec == QSIM_C64 ? 5 : 4);
     const int cap = std::min(b - L, kMaxTileHigh);
-    std::vector<int> rem(p->gates.size());
-    for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
     while (!rem.empty()) {
         uint64_t defN = 0, defA = 0, high = 0;
         int nh = 0;
@@ -892,6 +980,8 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
         } else if (st.type == S_TILE) {
             if (int rc = launch_tile_pass(dst, first ? src : dst, p->M, p->prec, st.d, p->d_ops, p->d_runs, s))
                 return rc;
+        } else if (st.type == S_PERM) {
+            if (int rc = launch_perm(dst, first ? src : dst, p->M, p->prec, st.perm, s)) return rc;
         } else if (st.type == S_FUSED) {
             if (int rc = launch_fused(dst, first ? src : dst, p->M, st.f, static_cast<const float *>(p->d_rimg) + st.rimg,
                                       p->d_status, s))
@@ -992,9 +1082,35 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
         if (prec == QSIM_C64) split_row_phases(p->gates);
         std::vector<unsigned char> runs;
         if (rc == QSIM_OK) {
+            // gate segments between runs of swaps; each swap run is one permutation pass
+            std::vector<int> run_of;
+            std::vector<std::vector<int>> perms;
+            find_swap_runs(p->gates, run_of, perms, M);
+            std::vector<std::vector<int>> segs(1);
+            std::vector<int> perm_after;  // perm_after[s] = permutation following segment s, or -1
+            for (size_t gi = 0; gi < p->gates.size(); ++gi) {
+                if (run_of[gi] < 0) {
+                    segs.back().push_back(int(gi));
+                } else if (gi == 0 || run_of[gi - 1] != run_of[gi]) {
+                    perm_after.push_back(run_of[gi]);
+                    segs.emplace_back();
+                }
+            }
+            perm_after.push_back(-1);
+            auto add_perm = [&](int s_idx) {
+                if (perm_after[size_t(s_idx)] < 0) return;
+                Step st{};
+                st.type = S_PERM;
+                st.perm = perm_desc(perms[size_t(perm_after[size_t(s_idx)])], M, prec);
+                st.bytes = 2.0 * std::ldexp(1.0, M) * double(amp_bytes(prec));
+                p->steps.push_back(st);
+            };
             if (prec == QSIM_C64) {
                 std::vector<TileOp<float2>> ops;
-                plan_tiled(p, b, ops, runs);
+                for (size_t si = 0; si < segs.size(); ++si) {
+                    plan_tiled(p, b, segs[si], ops, runs);
+                    add_perm(int(si));
+                }
                 std::vector<RegOp> regops;
                 std::vector<RoundDesc> rounds;
                 for (Step &st : p->steps) {  // register rounds where the tile size allows
@@ -1002,14 +1118,17 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
                     const int RB = st.d.b - kRegThreadBits;
                     if (RB < 3 || RB > 4) continue;
                     TilePassDesc d = st.d;
-                    if (build_rounds(ops, st.d.op_begin, st.d.op_count, d, RB, regops, rounds)) st.d = d;
+                    if (build_rounds(ops, st.d.op_begin, st.d.op_count, d, RB, regops, rounds, runs)) st.d = d;
                 }
                 rc = upload(p, &p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
                 if (rc == QSIM_OK) rc = upload(p, &p->d_regops, regops.data(), regops.size() * sizeof(RegOp), &p->regops_bytes);
                 if (rc == QSIM_OK) rc = upload(p, &p->d_rounds, rounds.data(), rounds.size() * sizeof(RoundDesc), &p->rounds_bytes);
             } else {
                 std::vector<TileOp<double2>> ops;
-                plan_tiled(p, b, ops, runs);
+                for (size_t si = 0; si < segs.size(); ++si) {
+                    plan_tiled(p, b, segs[si], ops, runs);
+                    add_perm(int(si));
+                }
                 rc = upload(p, &p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
             }
         }

@@ -193,6 +193,19 @@ size_t fused_rimg_floats(int k);  // floats of one block's R_hi + R_lo image
 int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const float *rimg_dev, int *status,
                  cudaStream_t s);
 
+// ------------------------------------------------------- qubit permutation
+// out[pi(i)] = in[i] for an involution pi of the qubit positions (see
+// k_perm.cu).  Tile qubits: spos[0..ns) ascending (they include 0..4);
+// spi[j] = tile-local index of pi(spos[j]); outside qubits opos[0..nout)
+// ascending and opi[j] = outside index of pi(opos[j]).
+struct PermDesc {
+    int ns, nout, lb;  // tile qubits, outside qubits, low qubits per contiguous run
+    int spos[12], spi[12];
+    int opos[QSIM_MAX_QUBITS], opi[QSIM_MAX_QUBITS];
+};
+size_t perm_smem_bytes(const PermDesc &d, qsim_prec prec);  // at most 96 KiB
+int launch_perm(void *dst, const void *src, int M, qsim_prec prec, const PermDesc &d, cudaStream_t s);
+
 // -------------------------------------------------------------- reductions
 // Results land in scratch[result_offset .. +3): (norm, re <i|n>, im <i|n>).
 int launch_reduce(const void *ideal, const void *noisy, int M, qsim_prec prec, double *scratch,
