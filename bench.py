@@ -252,7 +252,8 @@ def run_ours(args, rank, world, local):
             d[0] += t_ms[j]
             d[1] += t_bytes[j] * execs
             d[2] += execs
-    kname = {0: "k_gate (one gate per launch)", 1: "k_tile_pass", 2: "k_fused_tc"}
+    kname = {0: "k_gate (one gate per launch)", 1: "k_tile_pass", 2: "k_fused_tc", 3: "k_permute",
+             4: "k_tile_reg"}
     top = max(kinds, key=lambda k: kinds[k][0])
     tot_ms, tot_bytes, n_launch = kinds[top]
     peak, peak_src = measured_peaks()

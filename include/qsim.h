@@ -83,7 +83,8 @@ typedef enum {
 
 typedef struct qsim_opts {
     int32_t mode;       /* qsim_mode */
-    int32_t fuse_k;     /* QSIM_MODE_FUSED block width 2..5; 0 = default */
+    int32_t fuse_k;     /* QSIM_MODE_FUSED block width 2..5 (2 runs as 3); 0 = default (5).  The fused
+                         * mode needs complex64 and M >= 12, and falls back to TILED otherwise */
     int32_t tile_bits;  /* QSIM_MODE_TILED tile size 2^tile_bits amplitudes, 6..13; 0 = default */
     int32_t use_graph;  /* 1: a plan replays its launches as one captured CUDA graph */
 } qsim_opts;
@@ -188,7 +189,8 @@ int qsim_plan_set_timing(qsim_plan *plan, int enable);
 /* Wait for the recorded events and report, for each launch index j < n_max
  * of one execution: ms[j] = milliseconds summed over the timed executions,
  * bytes[j] = algorithmic bytes of that launch, kind[j] = 0 single gate,
- * 1 tile pass, 2 fused block.  *executions = number of timed executions.
+ * 1 shared-memory tile pass, 2 fused block, 3 qubit permutation pass,
+ * 4 register tile pass (complex64).  *executions = number of timed executions.
  * Any output array may be NULL.  Clears the record. */
 int qsim_plan_timing(qsim_plan *plan, int64_t n_max, double *ms, double *bytes, int32_t *kind,
                      int64_t *executions);

@@ -1,4 +1,4 @@
-// Fused dense blocks on the tensor cores (tcgen05, kind::tf32).
+// Fused dense blocks on the tensor cores (tcgen05, kind::f16, FP32 accumulate).
 //
 // Section 2.1 applies a 2x2 block to every pair of states that differ in one
 // bit.  A run of gates acting on k qubits B = {b_0 < ... < b_{k-1}} multiplies
@@ -11,47 +11,64 @@
 // matrix product D (128 x 2^(k+1)) = X (128 x 2^(k+1)) R^T: the one dense
 // contraction of the simulator, run on the tensor cores.
 //
-// Precision: complex64 amplitudes, FP32 accumulation.  TF32 keeps 11
-// significant bits, so both operands are split, v = hi + lo with hi and lo
-// rounded to TF32 (to nearest), and D = X_lo R_hi + X_hi R_lo + X_hi R_hi
-// (the lo*lo term is below 2^-22 relative).  The tensor core's FP32
-// accumulation truncates, which shrinks every output by a fraction of an ulp
-// on average; over many blocks that bias would show in the norm and the
-// fidelity.  A unitary block preserves the norm of every sub-vector, so for
-// blocks the planner has checked to be unitary the epilogue rescales each
-// output sub-vector to its input norm (sums in FP32, rounded to nearest; the
-// correction applied as v + v c with c = (|x|^2 - |y|^2) / (2 |y|^2)), which
-// removes the bias and leaves unbiased rounding.
+// Precision: complex64 amplitudes, FP32 accumulation.  Both operands are
+// split into FP16 pairs, v = hi + lo (11 + 11 significant bits), and
+// D = X_lo R_hi + X_hi R_lo + X_hi R_hi (the lo*lo term is below 2^-22
+// relative).  FP16 has a narrow exponent range, so every sub-vector is scaled
+// by a power of two that puts its largest component just below 2^15 before
+// the split (and R by 2^8); the epilogue multiplies the scale back out, which
+// is exact.  The tensor core's FP32 accumulation truncates, which shrinks
+// every output by a fraction of an ulp on average; over many blocks that bias
+// would show in the norm and the fidelity.  A unitary block preserves the norm
+// of every sub-vector, so for blocks the planner has checked to be unitary the
+// epilogue rescales each output sub-vector to its input norm (the correction
+// applied as v + v c with c = (|x|^2 - |y|^2) / (2 |y|^2)), which removes the
+// bias and leaves unbiased rounding.
 //
-// Tile: the k block qubits plus F = the 7 lowest other qubits, 2^(k+7)
-// amplitudes, numbered by a tile-local index u whose bits are the qubits of
+// Tile: the k block qubits plus F = the 12 - k lowest other qubits, 4096
+// amplitudes numbered by a tile-local index u whose bits are the qubits of
 // B u F in ascending order.  B u F always holds qubits 0..6, so a tile is a
-// set of contiguous runs of >= 128 amplitudes, moved by bulk TMA copies
-// (cp.async.bulk) into and out of shared memory.  Sub-vector m (0..127) and
-// block combination a (0..2^k-1) sit at u = posA[a] | posM[m].
+// set of contiguous runs of >= 128 amplitudes, loaded by bulk TMA copies
+// (cp.async.bulk).  Sub-vector m (0 .. 2^(12-k) - 1) and block combination a
+// sit at u = posA[a] | posM[m]; the 2^(12-k) sub-vectors form 2^(5-k) MMA
+// row blocks of 128.
 //
-// Per CTA (persistent over tiles, 256 threads):
-//   load   one thread issues the bulk copies of a tile two tiles ahead
-//          (three tile buffers), completion on an mbarrier;
-//   split  all threads turn the tile into X_hi and X_lo in the canonical
-//          K-major 128-byte-swizzled layout that the MMA descriptors read;
-//   mma    one thread issues 3 x 2^(k+1)/8 tcgen05.mma (M=128, N=2^(k+1),
-//          K=8) into a TMEM accumulator and commits to an mbarrier;
-//   store  8 warps read the accumulator (tcgen05.ld, each warp its 32 TMEM
-//          lanes and half the columns), write the tile buffer back in tile
-//          order, and one thread issues the bulk stores.
+// Per CTA (persistent over tiles, one per SM, 320 threads), warp-specialised
+// and pipelined over tiles:
+//   warp 0       producer: bulk copies of a tile into one of 3 input stages;
+//   warp 1       MMA: 12 tcgen05.mma per tile (3 products x row blocks x
+//                K steps of 16) into one of 2 TMEM accumulators (64 columns
+//                each), committed to mbarriers;
+//   warps 2..5   split: each thread owns one sub-vector row per row block,
+//                reads its 2^k amplitudes (in a lane-skewed order, so the
+//                warp's reads and writes fall on distinct banks), scales,
+//                splits and writes X_hi, X_lo into one of 2 operand stages in
+//                the canonical K-major swizzled layout the MMA reads;
+//   warps 6..9   epilogue: each thread reads its row of the accumulator
+//                (tcgen05.ld), removes the scale, renormalises, writes the
+//                amplitudes into an XOR-swizzled staging tile, and the four
+//                warps then copy the staging tile to device memory in
+//                coalesced runs.
 // Every mbarrier wait is bounded (2 s of globaltimer); on a timeout the CTA
-// records QSIM_ETIMEOUT in the status word, waits (bounded) for its copies in
-// flight, frees its TMEM and returns.
+// records QSIM_ETIMEOUT in the status word, the other roles leave their loops,
+// the producer waits (bounded) for its copies in flight, the MMA warp for its
+// last commit, and the CTA frees its TMEM and returns.
+#include <cuda_fp16.h>
+
 #include "cx.cuh"
 #include "qsim_internal.h"
 
 namespace qs {
 namespace {
 
-constexpr int kMT = 128;       // sub-vectors per tile (MMA M)
-constexpr int kThreads = 256;  // 8 warps
-constexpr int kNBuf = 3;       // tile buffers
+constexpr int kThreads = 320;  // 10 warps
+constexpr int kNIn = 3;        // input stages
+constexpr int kNA = 2;         // operand stages = accumulator stages
+constexpr int kTileAmps = 1 << kFusedTileBits;
+constexpr uint32_t kInBytes = kTileAmps * 8;
+constexpr uint32_t kABytes = kTileAmps * 4;  // one of X_hi / X_lo for the whole tile (FP16 pairs)
+constexpr uint32_t kAccCols = 64;            // TMEM columns of one accumulator stage
+constexpr uint32_t kTmemCols = kNA * kAccCols;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -69,6 +86,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -80,13 +100,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait on an mbarrier phase; false once kWaitNs have passed.
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase; false once kWaitNs have passed or the
+// CTA is aborting.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, const volatile int *abort) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
         if (globaltimer() - t0 > kWaitNs) return false;
+    }
     return true;
+}
+// The same wait by every lane of a warp, with one outcome for all of them
+// (the warp stays converged for the .sync.aligned tcgen05 instructions).
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort)) != 0;
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -94,14 +122,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -116,21 +136,24 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (the swizzle atom), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
-           (uint64_t(1) << 46) | (uint64_t(2) << 61);
+// Shared-memory matrix descriptor, K-major, swizzled rows of W bytes
+// (W = 128, 64 or 32: layout 2, 4 or 6), 8-row groups 8 W bytes apart,
+// descriptor version 1.
+template <int W>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+    constexpr uint64_t layout = W == 128 ? 2 : (W == 64 ? 4 : 6);
+    return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t((8 * W) >> 4) << 32) |
+           (uint64_t(1) << 46) | (layout << 61);
 }
-// Instruction descriptor of kind::tf32: D f32, A and B tf32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+// Instruction descriptor of kind::f16: D f32, A and B f16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
@@ -140,112 +163,112 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// 32 lanes x 32 consecutive 32-bit columns of TMEM: thread = lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 32 lanes x N consecutive 32-bit columns of TMEM (thread = lane), issued
+// without waiting; tmem_wait_ld completes every load issued before it.
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float *v);
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float *v) {
+    uint32_t *r = reinterpret_cast<uint32_t *>(v);
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float *v) {
+    tmem_ld<16>(taddr, v);
+    tmem_ld<16>(taddr + 16, v + 16);
+}
+template <>
+__device__ __forceinline__ void tmem_ld<64>(uint32_t taddr, float *v) {
+    tmem_ld<32>(taddr, v);
+    tmem_ld<32>(taddr + 32, v + 32);
+}
+// Completes every TMEM load issued before it; the empty statements after it
+// tie the loaded registers to this point, so no use moves above the wait.
+template <int N>
+__device__ __forceinline__ void tmem_wait_ld(float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    for (int i = 0; i < N; i += 8)
+        asm volatile("" : "+f"(v[i]), "+f"(v[i + 1]), "+f"(v[i + 2]), "+f"(v[i + 3]), "+f"(v[i + 4]), "+f"(v[i + 5]),
+                     "+f"(v[i + 6]), "+f"(v[i + 7]));
 }
 
 template <int KF>
 struct Cfg {
-    static constexpr int NA = 1 << KF;                // amplitudes per sub-vector
-    static constexpr int KR = 2 * NA;                 // reals per sub-vector (MMA K and N)
-    static constexpr int TILE = NA * kMT;             // amplitudes per tile
-    static constexpr uint32_t A_BYTES = kMT * KR * 4;  // one X operand (hi or lo)
-    static constexpr uint32_t A_CHUNK = kMT * 128;     // one 128-byte K chunk of X
-    static constexpr uint32_t B_BYTES = KR * KR * 4;   // one R operand
-    static constexpr uint32_t B_CHUNK = KR * 128;
-    static constexpr uint32_t IN_BYTES = TILE * 8;
-    static constexpr uint32_t TMEM_COLS = KR < 32 ? 32 : KR;
-    static constexpr uint32_t SMEM = 1024 + 2 * A_BYTES + 2 * B_BYTES + kNBuf * IN_BYTES;
+    static constexpr int NA = 1 << KF;                 // amplitudes per sub-vector
+    static constexpr int KR = 2 * NA;                  // reals per sub-vector (MMA K and N)
+    static constexpr int W = KR * 2;                   // bytes of one operand row (FP16)
+    static constexpr int NRB = 1 << (5 - KF);          // row blocks of 128 sub-vectors per tile
+    static constexpr int NROWS = 128 * NRB;            // sub-vectors per tile
+    static constexpr uint32_t RB_BYTES = 128 * W;      // one row block of one operand
+    static constexpr uint32_t B_BYTES = KR * KR * 2;   // one of R_hi / R_lo
+    static constexpr int KSTEPS = KR / 16;             // MMA K = 16 (32 bytes)
+    // dynamic shared memory: inputs, operands (hi, lo per stage), R, staging
+    static constexpr uint32_t OFF_IN = 0;
+    static constexpr uint32_t OFF_A = OFF_IN + kNIn * kInBytes;
+    static constexpr uint32_t OFF_B = OFF_A + kNA * 2 * kABytes;
+    static constexpr uint32_t OFF_OUT = OFF_B + 2 * (B_BYTES < 1024 ? 1024 : B_BYTES);
+    static constexpr uint32_t SMEM = 1024 + OFF_OUT + kInBytes;
 };
 
 struct SmemCtl {
-    uint64_t bar_load[kNBuf];
-    uint64_t bar_mma;
+    uint64_t full_in[kNIn], empty_in[kNIn];
+    uint64_t full_a[kNA], empty_a[kNA];
+    uint64_t full_acc[kNA], empty_acc[kNA];
     uint64_t bar_r;
-    uint64_t runoff[32];
+    uint64_t epi_full, epi_free;          // staging tile written / copied out (4 epilogue warps)
+    uint64_t gofs[32];                    // device offset of tile-local index 128 j, this tile (epilogue)
     uint32_t tmem;
     int abort;
-    uint16_t posA[32];
-    uint16_t posM[kMT];
-    uint8_t decA[2][64];  // a = decA[0][u & 63] | decA[1][u >> 6]
-    uint8_t decM[2][64];  // m = decM[0][u & 63] | decM[1][u >> 6]
-    float2 red[2][kMT];   // per row and column half: (|x|^2, |y|^2)
+    uint32_t swA8[32];                    // 8 * swz(posA[a]): staging byte offset of combination a
+    uint16_t posM[1 << kFusedRowBits];    // u of sub-vector m
+    float2 rowinfo[kNA][1 << kFusedRowBits];  // per sub-vector: (|x|^2, 1 / total scale)
 };
+
+// XOR swizzle of the staging tile (8-byte amplitudes): bits [0,4) ^= bits [r, r+4).
+__device__ __forceinline__ uint32_t stg_swz(uint32_t u, int r) { return u ^ ((u >> r) & 15u); }
 
 template <int KF>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_fused_tc(float2 *dst, const float2 *src, FusedDesc d, const float *__restrict__ rimg, uint64_t ntiles,
+    k_fused_tc(float2 *dst, const float2 *src, FusedDesc d, const __half *__restrict__ rimg, uint64_t ntiles,
                int *status) {
     using C = Cfg<KF>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float *Ahi = reinterpret_cast<float *>(sm);
-    float *Alo = reinterpret_cast<float *>(sm + C::A_BYTES);
-    float *Bhi = reinterpret_cast<float *>(sm + 2 * C::A_BYTES);
-    float *Blo = reinterpret_cast<float *>(sm + 2 * C::A_BYTES + C::B_BYTES);
-    float2 *IN = reinterpret_cast<float2 *>(sm + 2 * C::A_BYTES + 2 * C::B_BYTES);
     __shared__ SmemCtl ctl;
+    volatile int *abort = &ctl.abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nrun = 1 << d.nrb;
     const uint32_t run_amps = 1u << d.runbits;
-    if (tid < C::NA) ctl.posA[tid] = d.posA[tid];
-    if (tid < kMT) ctl.posM[tid] = d.posM[tid];
-    if (tid < 64) {
-        ctl.decA[0][tid] = d.decA[0][tid];
-        ctl.decA[1][tid] = d.decA[1][tid];
-        ctl.decM[0][tid] = d.decM[0][tid];
-        ctl.decM[1][tid] = d.decM[1][tid];
-    }
-    if (tid < nrun) {
-        uint64_t off = 0;
-        for (int i = 0; i < d.nrb; ++i)
-            if ((tid >> i) & 1) off |= uint64_t(1) << d.rpos[i];
-        ctl.runoff[tid] = off;
-    }
+    for (int m = tid; m < C::NROWS; m += kThreads) ctl.posM[m] = d.posM[m];
+    if (tid < C::NA) ctl.swA8[tid] = 8u * stg_swz(d.posA[tid], d.outsh);
     if (tid == 0) {
-        for (int b = 0; b < kNBuf; ++b) mbar_init(&ctl.bar_load[b], 1);
-        mbar_init(&ctl.bar_mma, 1);
+        for (int b = 0; b < kNIn; ++b) {
+            mbar_init(&ctl.full_in[b], 1);
+            mbar_init(&ctl.empty_in[b], 4);
+        }
+        for (int b = 0; b < kNA; ++b) {
+            mbar_init(&ctl.full_a[b], 4);
+            mbar_init(&ctl.empty_a[b], 1);
+            mbar_init(&ctl.full_acc[b], 1);
+            mbar_init(&ctl.empty_acc[b], 4);
+        }
         mbar_init(&ctl.bar_r, 1);
+        mbar_init(&ctl.epi_full, 4);
+        mbar_init(&ctl.epi_free, 4);
         ctl.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(&ctl.tmem, C::TMEM_COLS);
+    if (warp == 1) tmem_alloc(&ctl.tmem, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = ctl.tmem;
-
     const uint64_t n_local = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     auto tile_base = [&](uint64_t i) {
         const uint64_t tile = blockIdx.x + i * gridDim.x;
@@ -254,139 +277,251 @@ __global__ void __launch_bounds__(kThreads, 1)
             if ((tile >> j) & 1) base |= uint64_t(1) << d.opos[j];
         return base;
     };
-    auto issue_load = [&](uint64_t i) {  // thread 0 only
-        const int b = int(i % kNBuf);
-        const uint64_t base = tile_base(i);
-        float2 *buf = IN + size_t(b) * C::TILE;
-        mbar_expect_tx(&ctl.bar_load[b], C::IN_BYTES);
-        for (int r = 0; r < nrun; ++r)
-            bulk_g2s(buf + size_t(r) * run_amps, src + base + ctl.runoff[r], run_amps * 8, &ctl.bar_load[b]);
-    };
+    bool ok = true;
 
-    uint64_t issued = 0;  // tiles whose load was issued
-    if (tid == 0) {
-        mbar_expect_tx(&ctl.bar_r, 2 * C::B_BYTES);
-        bulk_g2s(Bhi, rimg, C::B_BYTES, &ctl.bar_r);
-        bulk_g2s(Blo, rimg + C::B_BYTES / 4, C::B_BYTES, &ctl.bar_r);
-        for (; issued < n_local && issued < kNBuf - 1; ++issued) issue_load(issued);
-    }
-    bool ok = mbar_wait(&ctl.bar_r, 0);
-    constexpr uint32_t IDESC = idesc_tf32(kMT, C::KR);
-
-    for (uint64_t i = 0; ok && i < n_local; ++i) {
-        const int b = int(i % kNBuf);
-        float2 *buf = IN + size_t(b) * C::TILE;
-        ok = mbar_wait(&ctl.bar_load[b], uint32_t((i / kNBuf) & 1));
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-
-        // split: tile order -> X_hi, X_lo (row m, column 2a + re/im), swizzled
-        for (int u = tid * 2; u < C::TILE; u += kThreads * 2) {
-            const float4 v = *reinterpret_cast<const float4 *>(buf + u);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int uu = u + h;
-                const int a = ctl.decA[0][uu & 63] | ctl.decA[1][uu >> 6];
-                const int m = ctl.decM[0][uu & 63] | ctl.decM[1][uu >> 6];
-                const float re = h ? v.z : v.x, im = h ? v.w : v.y;
-                const float rh = tf32_rna(re), ih = tf32_rna(im);
-                const float rl = tf32_rna(re - rh), il = tf32_rna(im - ih);
-                const int kk = 2 * a;
-                const uint32_t off = uint32_t(kk >> 5) * C::A_CHUNK + uint32_t(m >> 3) * 1024 + uint32_t(m & 7) * 128 +
-                                     uint32_t((((kk & 31) >> 2) ^ (m & 7)) << 4) + uint32_t((kk & 3) << 2);
-                *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(Ahi) + off) = make_float2(rh, ih);
-                *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(Alo) + off) = make_float2(rl, il);
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        uint64_t issued = 0;
+        if (lane == 0) {
+            unsigned char *Bs = sm + C::OFF_B;
+            const uint32_t bstride = C::B_BYTES < 1024 ? 1024 : C::B_BYTES;
+            mbar_expect_tx(&ctl.bar_r, 2 * C::B_BYTES);
+            bulk_g2s(Bs, rimg, C::B_BYTES, &ctl.bar_r);
+            bulk_g2s(Bs + bstride, rimg + C::B_BYTES / 2, C::B_BYTES, &ctl.bar_r);
+            for (uint64_t i = 0; i < n_local; ++i) {
+                const int s = int(i % kNIn);
+                if (i >= kNIn && !mbar_wait(&ctl.empty_in[s], uint32_t(((i / kNIn) & 1) ^ 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                const uint64_t base = tile_base(i);
+                float2 *buf = reinterpret_cast<float2 *>(sm + C::OFF_IN + size_t(s) * kInBytes);
+                mbar_expect_tx(&ctl.full_in[s], kInBytes);
+                for (int r = 0; r < nrun; ++r) {
+                    uint64_t off = 0;
+                    for (int b = 0; b < d.nrb; ++b)
+                        if ((r >> b) & 1) off |= uint64_t(1) << d.rpos[b];
+                    bulk_g2s(buf + size_t(r) * run_amps, src + base + off, run_amps * 8, &ctl.full_in[s]);
+                }
+                issued = i + 1;
+            }
+            if (!ok) {
+                atomicExch(status, QSIM_ETIMEOUT);
+                ctl.abort = 1;
+            }
+            // the copies of the last stages may still be landing if a consumer left early
+            const uint64_t first = issued > kNIn ? issued - kNIn : 0;
+            for (uint64_t j = first; j < issued; ++j) {
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(&ctl.full_in[j % kNIn], uint32_t((j / kNIn) & 1)))
+                    if (globaltimer() - t0 > kWaitNs) break;
+            }
+            {
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(&ctl.bar_r, 0))
+                    if (globaltimer() - t0 > kWaitNs) break;
             }
         }
-        fence_proxy_async();
-        __syncthreads();
-
-        if (tid == 0) {
+        __syncwarp();
+    } else if (warp == 1) {
+        // ----------------------------------------------------------------- MMA
+        uint64_t done = 0;  // tiles whose MMAs were issued
+        if (lane == 0) {
+            ok = mbar_wait(&ctl.bar_r, 0, abort);
+            const uint32_t bh = smem_u32(sm + C::OFF_B);
+            const uint32_t bl = bh + (C::B_BYTES < 1024 ? 1024 : C::B_BYTES);
+            constexpr uint32_t IDESC = idesc_f16(128, C::KR);
+            for (uint64_t i = 0; ok && i < n_local; ++i) {
+                const int t = int(i % kNA);
+                const uint32_t ph = uint32_t((i / kNA) & 1);
+                if (!mbar_wait(&ctl.full_a[t], ph, abort)) { ok = false; break; }
+                if (i >= kNA && !mbar_wait(&ctl.empty_acc[t], ph ^ 1, abort)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t ah = smem_u32(sm + C::OFF_A + uint32_t(t) * 2 * kABytes);
+                const uint32_t al = ah + kABytes;
+                const uint32_t As[3] = {al, ah, ah}, Bs[3] = {bh, bl, bh};  // small products first
+#pragma unroll
+                for (int rb = 0; rb < C::NRB; ++rb) {
+                    const uint32_t dcol = tmem + uint32_t(t) * kAccCols + uint32_t(rb * C::KR);
+#pragma unroll
+                    for (int pr = 0; pr < 3; ++pr) {
+#pragma unroll
+                        for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                            const uint64_t ad = sw_desc<C::W>(As[pr] + uint32_t(rb) * C::RB_BYTES + uint32_t(ks) * 32);
+                            const uint64_t bd = sw_desc<C::W>(Bs[pr] + uint32_t(ks) * 32);
+                            mma_f16(dcol, ad, bd, IDESC, (pr | ks) != 0);
+                        }
+                    }
+                }
+                mma_commit(&ctl.empty_a[t]);
+                mma_commit(&ctl.full_acc[t]);
+                done = i + 1;
+            }
+            if (!ok) {
+                atomicExch(status, QSIM_ETIMEOUT);
+                ctl.abort = 1;
+            }
+            if (done > 0) {  // the last MMAs must be complete before TMEM is freed
+                const uint64_t j = done - 1;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(&ctl.empty_a[j % kNA], uint32_t((j / kNA) & 1)))
+                    if (globaltimer() - t0 > kWaitNs) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp < 6) {
+        // --------------------------------------------------------------- split
+        const int sw = warp - 2;
+        const uint32_t g = d.skew[lane];
+        const uint32_t pAg = d.posA[g];
+        uint32_t posA8[C::NA];
+#pragma unroll
+        for (int a = 0; a < C::NA; ++a) posA8[a] = 8u * d.posA[a];
+        for (uint64_t i = 0; i < n_local; ++i) {
+            const int s_in = int(i % kNIn), t = int(i % kNA);
+            const uint32_t ph = uint32_t((i / kNA) & 1);
+            ok = warp_wait(&ctl.full_in[s_in], uint32_t((i / kNIn) & 1), abort);
+            if (ok && i >= kNA) ok = warp_wait(&ctl.empty_a[t], ph ^ 1, abort);
+            if (ok && i >= kNA) ok = warp_wait(&ctl.empty_acc[t], ph ^ 1, abort);
+            if (!ok) break;
+            const unsigned char *in = sm + C::OFF_IN + size_t(s_in) * kInBytes;
+            unsigned char *ahi = sm + C::OFF_A + uint32_t(t) * 2 * kABytes;
+#pragma unroll 1
+            for (int rb = 0; rb < C::NRB; ++rb) {
+                const int rho = 32 * sw + lane;
+                const int m = rb * 128 + rho;
+                const uint32_t lin = 8u * (pAg ^ ctl.posM[m]);
+                float2 x[C::NA];
+                float mx = 0.f;
+#pragma unroll
+                for (int s = 0; s < C::NA; ++s) {
+                    x[s] = *reinterpret_cast<const float2 *>(in + (posA8[s] ^ lin));
+                    mx = fmaxf(mx, fmaxf(fabsf(x[s].x), fabsf(x[s].y)));
+                }
+                // scale 2^es puts the largest component in [2^14, 2^15); rows below
+                // 2^-104 keep es = 118, so that 2^-es-8 stays a normal float
+                const int e = int((__float_as_uint(mx) >> 23) & 255u) - 127;
+                int es = 14 - e;
+                if (es > 118) es = 118;
+                const float scale = __uint_as_float(uint32_t(es + 127) << 23);
+                const float inv = __uint_as_float(uint32_t(127 - es - 8) << 23);  // 2^-es * 2^-8 (R's scale)
+                float sx = 0.f;  // |x|^2 in scaled units (no overflow or underflow)
+                // operand row rho of row block rb: amplitude a at bytes 4a, 16-byte chunks swizzled
+                uint32_t swr;
+                if constexpr (C::W == 128) swr = uint32_t(rho & 7);
+                else if constexpr (C::W == 64) swr = uint32_t((rho >> 1) & 3);
+                else swr = uint32_t((rho >> 2) & 1);
+                const uint32_t cl = (uint32_t(rho) * C::W) ^ (swr << 4) ^ (4u * g);
+                unsigned char *rowb = ahi + uint32_t(rb) * C::RB_BYTES;
+#pragma unroll
+                for (int s = 0; s < C::NA; ++s) {
+                    const float2 xs = make_float2(x[s].x * scale, x[s].y * scale);
+                    sx = fmaf(xs.x, xs.x, fmaf(xs.y, xs.y, sx));
+                    const __half2 h = __float22half2_rn(xs);
+                    const float2 hf = __half22float2(h);
+                    const __half2 l = __float22half2_rn(make_float2(xs.x - hf.x, xs.y - hf.y));
+                    const uint32_t off = cl ^ (4u * uint32_t(s));
+                    *reinterpret_cast<__half2 *>(rowb + off) = h;
+                    *reinterpret_cast<__half2 *>(rowb + kABytes + off) = l;
+                }
+                ctl.rowinfo[t][m] = make_float2(sx, inv);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl.empty_in[s_in]);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl.full_a[t]);
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(status, QSIM_ETIMEOUT);
+            ctl.abort = 1;
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int qd = warp & 3;  // TMEM lane quadrant of this warp
+        const int te = tid - 6 * 32;  // 0..127
+        const unsigned char *outb = sm + C::OFF_OUT;
+        for (uint64_t i = 0; i < n_local; ++i) {
+            const int t = int(i % kNA);
+            ok = warp_wait(&ctl.full_acc[t], uint32_t((i / kNA) & 1), abort);
+            // the split's row data of this tile (complete, as the MMAs that read its operands are)
+            if (ok) ok = warp_wait(&ctl.full_a[t], uint32_t((i / kNA) & 1), abort);
+            if (!ok) break;
             tc_fence_after();
-            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-            const uint32_t As[3] = {al, ah, ah}, Bs[3] = {bh, bl, bh};  // small products first
+            const int rho = 32 * qd + lane;
+            float y[C::NRB][C::KR];
+            float2 ri[C::NRB];
 #pragma unroll
-            for (int pr = 0; pr < 3; ++pr) {
+            for (int rb = 0; rb < C::NRB; ++rb) {
+                ri[rb] = ctl.rowinfo[t][rb * 128 + rho];
+                tmem_ld<C::KR>(tmem + (uint32_t(32 * qd) << 16) + uint32_t(t) * kAccCols + uint32_t(rb * C::KR), y[rb]);
+            }
+            tmem_wait_ld<C::NRB * C::KR>(&y[0][0]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl.empty_acc[t]);
 #pragma unroll
-                for (int ks = 0; ks < C::KR / 8; ++ks) {
-                    const uint32_t koff = uint32_t(ks & 3) * 32;
-                    const uint64_t ad = sw128_desc(As[pr] + uint32_t(ks >> 2) * C::A_CHUNK + koff);
-                    const uint64_t bd = sw128_desc(Bs[pr] + uint32_t(ks >> 2) * C::B_CHUNK + koff);
-                    mma_tf32(tmem, ad, bd, IDESC, (pr | ks) != 0);
+            for (int rb = 0; rb < C::NRB; ++rb) {
+                float sy = 0.f;  // in the split's scaled units: the accumulator carries R's 2^8 too
+#pragma unroll
+                for (int j = 0; j < C::KR; ++j) {
+                    const float ys = y[rb][j] * (1.0f / 256.0f);
+                    sy = fmaf(ys, ys, sy);
+                    y[rb][j] *= ri[rb].y;
+                }
+                if (d.unitary) {
+                    const float sx = ri[rb].x;
+                    // sqrt(sx/sy) - 1 to first order, kept as a small number: the
+                    // bias is a fraction of an ulp, so a scale factor near 1 would
+                    // round to exactly 1; v + v c rounds to nearest, unbiased.
+                    const float c = (sx > 0.f && sy > 0.f) ? (sx - sy) / (2.f * sy) : 0.f;
+#pragma unroll
+                    for (int j = 0; j < C::KR; ++j) y[rb][j] = fmaf(y[rb][j], c, y[rb][j]);
                 }
             }
-            mma_commit(&ctl.bar_mma);
-            // the store of tile i-1 must have read its buffer before tile i+2 lands in it
-            bulk_wait_read_all();
-            if (issued < n_local) issue_load(issued++);
-        }
-        ok = mbar_wait(&ctl.bar_mma, uint32_t(i & 1));
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        tc_fence_after();
-
-        // epilogue: warp w reads TMEM lanes 32(w%4).. (rows m) and half the columns
-        {
-            const int m = 32 * (warp & 3) + lane;
-            const int half = warp >> 2;
-            const uint32_t taddr = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(half * (C::KR / 2));
-            const uint32_t pm = ctl.posM[m];
-            constexpr int NJ = C::KR / 4;  // amplitudes per thread
-            float sx = 0.f;
-            if (d.unitary) {
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) {
-                    const float2 x = buf[ctl.posA[half * NJ + j] | pm];
-                    sx = fmaf(x.x, x.x, fmaf(x.y, x.y, sx));
-                }
+            if (i > 0 && !warp_wait(&ctl.epi_free, uint32_t((i - 1) & 1), abort)) {  // staging copied out
+                ok = false;
+                break;
             }
-            float v[2 * NJ];
-            if constexpr (NJ == 16)
-                tmem_ld32(taddr, v);
-            else
-                tmem_ld16(taddr, v);
-            if (d.unitary) {
-                float sy = 0.f;
-#pragma unroll
-                for (int j = 0; j < 2 * NJ; ++j) sy = fmaf(v[j], v[j], sy);
-                ctl.red[half][m] = make_float2(sx, sy);
-                __syncthreads();
-                const float tx = ctl.red[0][m].x + ctl.red[1][m].x;
-                const float ty = ctl.red[0][m].y + ctl.red[1][m].y;
-                // sqrt(tx/ty) - 1 to first order, kept as a small number: the
-                // bias is a fraction of an ulp, so a scale factor near 1 would
-                // round to exactly 1; v + v c rounds to nearest, unbiased.
-                const float c = (tx > 0.f && ty > 0.f) ? (tx - ty) / (2.f * ty) : 0.f;
-#pragma unroll
-                for (int j = 0; j < 2 * NJ; ++j) v[j] = fmaf(v[j], c, v[j]);
+            if (warp == 6) {
+                const uint64_t base = tile_base(i);
+                ctl.gofs[lane] = base | d.runoff2[lane];
             }
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) buf[ctl.posA[half * NJ + j] | pm] = make_float2(v[2 * j], v[2 * j + 1]);
+            for (int rb = 0; rb < C::NRB; ++rb) {
+                const uint32_t swm = 8u * stg_swz(ctl.posM[rb * 128 + rho], d.outsh);
+#pragma unroll
+                for (int a = 0; a < C::NA; ++a)
+                    *reinterpret_cast<float2 *>(const_cast<unsigned char *>(outb) + (ctl.swA8[a] ^ swm)) =
+                        make_float2(y[rb][2 * a], y[rb][2 * a + 1]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl.epi_full);
+            if (!warp_wait(&ctl.epi_full, uint32_t(i & 1), abort)) {
+                ok = false;
+                break;
+            }
+            const uint32_t swt = stg_swz(uint32_t(te), d.outsh);
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                // u = te + 128 j; staging index swz(u) = swz(te) ^ swz(128 j)
+                const uint32_t su = swt ^ stg_swz(uint32_t(j) << 7, d.outsh);
+                const float2 v = *reinterpret_cast<const float2 *>(outb + 8u * su);
+                dst[ctl.gofs[j] + uint32_t(te)] = v;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl.epi_free);
         }
-        tc_fence_before();
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            const uint64_t base = tile_base(i);
-            for (int r = 0; r < nrun; ++r)
-                bulk_s2g(dst + base + ctl.runoff[r], buf + size_t(r) * run_amps, run_amps * 8);
-            bulk_commit();
+        if (!ok) {
+            if (lane == 0) atomicExch(status, QSIM_ETIMEOUT);
+            ctl.abort = 1;
         }
     }
 
-    if (!ok) {
-        if (tid == 0) atomicExch(status, QSIM_ETIMEOUT);
-        ctl.abort = 1;
-    }
-    if (tid == 0) {
-        // wait (bounded) for loads still in flight, then for the stores
-        const uint64_t n_consumed = ok ? n_local : 0;
-        for (uint64_t j = n_consumed; j < issued; ++j)
-            if (j + kNBuf >= issued) mbar_wait(&ctl.bar_load[j % kNBuf], uint32_t((j / kNBuf) & 1));
-        bulk_wait_all();
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, C::TMEM_COLS);
+    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace
@@ -396,27 +531,30 @@ int fused_prepare() {
     int dev = 0;
     QS_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && configured[dev]) return QSIM_OK;
+    QS_CUDA(cudaFuncSetAttribute(k_fused_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<3>::SMEM)));
     QS_CUDA(cudaFuncSetAttribute(k_fused_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<4>::SMEM)));
     QS_CUDA(cudaFuncSetAttribute(k_fused_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<5>::SMEM)));
     if (dev < 64) configured[dev] = 1;
     return QSIM_OK;
 }
 
-size_t fused_rimg_floats(int k) { return 2 * size_t(4) << (2 * k); }  // 2 x (2^(k+1))^2
+size_t fused_rimg_halves(int k) { return 2 * size_t(4) << (2 * k); }  // 2 x (2^(k+1))^2
 
-int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const float *rimg_dev, int *status,
+int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const void *rimg_dev, int *status,
                  cudaStream_t s) {
     if (int rc = fused_prepare()) return rc;
-    const uint64_t ntiles = uint64_t(1) << (M - d.k - 7);
-    const int per_sm = d.k == 4 ? 2 : 1;
-    uint64_t grid = uint64_t(num_sms()) * per_sm;
+    const uint64_t ntiles = uint64_t(1) << (M - kFusedTileBits);
+    uint64_t grid = uint64_t(num_sms());
     if (grid > ntiles) grid = ntiles;
-    if (d.k == 5)
-        k_fused_tc<5><<<unsigned(grid), kThreads, Cfg<5>::SMEM, s>>>(
-            static_cast<float2 *>(dst), static_cast<const float2 *>(src), d, rimg_dev, ntiles, status);
-    else
-        k_fused_tc<4><<<unsigned(grid), kThreads, Cfg<4>::SMEM, s>>>(
-            static_cast<float2 *>(dst), static_cast<const float2 *>(src), d, rimg_dev, ntiles, status);
+    float2 *o = static_cast<float2 *>(dst);
+    const float2 *i = static_cast<const float2 *>(src);
+    const __half *r = static_cast<const __half *>(rimg_dev);
+    switch (d.k) {
+        case 3: k_fused_tc<3><<<unsigned(grid), kThreads, Cfg<3>::SMEM, s>>>(o, i, d, r, ntiles, status); break;
+        case 4: k_fused_tc<4><<<unsigned(grid), kThreads, Cfg<4>::SMEM, s>>>(o, i, d, r, ntiles, status); break;
+        case 5: k_fused_tc<5><<<unsigned(grid), kThreads, Cfg<5>::SMEM, s>>>(o, i, d, r, ntiles, status); break;
+        default: set_error("fused block width %d outside [3, 5]", d.k); return QSIM_EINVAL;
+    }
     QS_CHECK_LAUNCH("fused tensor-core launch");
     return QSIM_OK;
 }

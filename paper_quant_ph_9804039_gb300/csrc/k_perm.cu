@@ -10,9 +10,10 @@
 // tile pi(o).  A block reads tile o and its partner, both as runs of 2^lb
 // contiguous amplitudes (every thread's loads of both tiles in flight at
 // once), and writes each into the other's place, reading shared memory in the
-// permuted order.  Rows of 2^lb amplitudes are padded by one amplitude, so
-// the transposed reads (2^lb apart) fall on distinct banks.  In place is
-// safe: a pair is read completely before it is written.
+// permuted order.  Shared memory holds amplitude u at u ^ ((u >> sh) & 15),
+// with the shift picked on the host so that both the writes in index order
+// and the permuted reads of a warp fall on distinct banks.  In place is safe:
+// a pair is read completely before it is written.
 #include "qsim_internal.h"
 
 namespace qs {
@@ -28,10 +29,9 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(T2 *dst, const T2 *src
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ns = d.ns, lb = d.lb;
     const uint32_t n = 1u << ns, lmask = (1u << lb) - 1, nh = n >> lb;
-    const uint32_t pn = n + nh;
     T2 *A = reinterpret_cast<T2 *>(smem_raw);
-    T2 *B = A + pn;
-    uint64_t *hoff = reinterpret_cast<uint64_t *>(B + pn);  // high local bits -> offset bits
+    T2 *B = A + n;
+    uint64_t *hoff = reinterpret_cast<uint64_t *>(B + n);  // high local bits -> offset bits
     uint32_t *slo = reinterpret_cast<uint32_t *>(hoff + nh);  // sig of the low / high local bits
     uint32_t *shi = slo + (lmask + 1);
     for (uint32_t u = threadIdx.x; u <= lmask || u < nh; u += blockDim.x) {
@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(T2 *dst, const T2 *src
         }
     }
     __syncthreads();
-    auto pad = [lb](uint32_t u) { return u + (u >> lb); };
+    const int sh = d.sh;
+    auto pad = [sh](uint32_t u) { return u ^ ((u >> sh) & 15u); };
     for (uint64_t o = blockIdx.x; o < ntiles; o += gridDim.x) {
         uint64_t o2 = 0, base = 0, base2 = 0;
         for (int j = 0; j < d.nout; ++j)
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(T2 *dst, const T2 *src
 template <typename T2>
 size_t perm_smem(const PermDesc &d) {
     const size_t n = size_t(1) << d.ns, nh = n >> d.lb, nl = size_t(1) << d.lb;
-    return 2 * (n + nh) * sizeof(T2) + nh * sizeof(uint64_t) + (nl + nh) * sizeof(uint32_t);
+    return 2 * n * sizeof(T2) + nh * sizeof(uint64_t) + (nl + nh) * sizeof(uint32_t);
 }
 
 template <typename T2>

@@ -103,36 +103,12 @@ __device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op) {
     }
 }
 
-template <int RB, bool SWAP, bool REAL, bool ALL>
-__device__ __forceinline__ void pairs_k(Slots<RB> &v, const RegOp &op) {
-    switch (op.k) {
-        case 0: pairs<RB, 0, SWAP, REAL, ALL>(v, op); break;
-        case 1: pairs<RB, 1, SWAP, REAL, ALL>(v, op); break;
-        case 2: pairs<RB, 2, SWAP, REAL, ALL>(v, op); break;
-        default: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL, ALL>(v, op); break;
-    }
-}
-
-// op.smask covering every pair (no control among the slot qubits) takes the
-// unconditional form.
-template <int RB, bool SWAP, bool REAL>
-__device__ __forceinline__ void pairs_any(Slots<RB> &v, const RegOp &op) {
-    uint32_t want = 0;  // lower slots of all pairs on slot bit k
-#pragma unroll
-    for (int c = 0; c < (1 << RB); ++c)
-        if (!((c >> op.k) & 1)) want |= 1u << c;
-    if (op.smask == want)
-        pairs_k<RB, SWAP, REAL, true>(v, op);
-    else
-        pairs_k<RB, SWAP, REAL, false>(v, op);
-}
-
 template <int RB>
 __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t i0, const RoundDesc &R,
                                          uint64_t base, uint64_t tile, const TilePassDesc &d,
                                          const unsigned char *__restrict__ runs, PhRunState &ps, int &nrun) {
     constexpr int S = 1 << RB;
-    if (op.kind == K_PHRUN) {  // every thread reaches the synchronisation inside
+    if (op.code == RC_PHRUN) {  // every thread reaches the synchronisation inside
         // Phi(i0 | slots c) = Phi(i0) + sum_{k in c} (cl[pos_k] + Q(i0 | bit_k) - Q(i0)) + Q(slots c):
         // five exponentials per thread, the slot-only factors e^{i Q(slots c)} precomputed.
         const unsigned char *rec = runs + op.gsel;
@@ -163,22 +139,31 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
     }
     if ((i0 & op.nmask) != op.nmask) return;  // a control (or the target) outside the slots is 0
     const uint32_t sm = op.smask;
-    switch (op.kind) {
-        case K_DENSE: pairs_any<RB, false, false>(v, op); break;
-        case K_RDENSE: pairs_any<RB, false, true>(v, op); break;
-        case K_SWAPX: pairs_any<RB, true, false>(v, op); break;
-        case K_PHASE1: {
-            if (sm == (1u << S) - 1) {
+#define QS_PAIR_CASES(BASE, SWAP, REAL)                                                   \
+    case BASE + 0: pairs<RB, 0, SWAP, REAL, true>(v, op); break;                          \
+    case BASE + 1: pairs<RB, 1, SWAP, REAL, true>(v, op); break;                          \
+    case BASE + 2: pairs<RB, 2, SWAP, REAL, true>(v, op); break;                          \
+    case BASE + 3: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL, true>(v, op); break;    \
+    case BASE + 4: pairs<RB, 0, SWAP, REAL, false>(v, op); break;                         \
+    case BASE + 5: pairs<RB, 1, SWAP, REAL, false>(v, op); break;                         \
+    case BASE + 6: pairs<RB, 2, SWAP, REAL, false>(v, op); break;                         \
+    case BASE + 7: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL, false>(v, op); break;
+    switch (op.code) {
+        QS_PAIR_CASES(RC_DENSE, false, false)
+        QS_PAIR_CASES(RC_RDENSE, false, true)
+        QS_PAIR_CASES(RC_SWAP, true, false)
+        case RC_PHASE_ALL: {
 #pragma unroll
-                for (int c = 0; c < S; ++c) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
-            } else {
-#pragma unroll
-                for (int c = 0; c < S; ++c)
-                    if ((sm >> c) & 1u) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
-            }
+            for (int c = 0; c < S; ++c) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
             break;
         }
-        case K_DIAG: {
+        case RC_PHASE: {
+#pragma unroll
+            for (int c = 0; c < S; ++c)
+                if ((sm >> c) & 1u) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
+            break;
+        }
+        case RC_DIAG: {
             const bool up_thread = (i0 & op.tbn) != 0;
 #pragma unroll
             for (int c = 0; c < S; ++c) {
@@ -188,7 +173,7 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
             }
             break;
         }
-        case K_SCALE: {
+        case RC_SCALE: {
             const bool up = (base & op.gsel) != 0;
             const float2 f = up ? op.u[3] : op.u[0], fl = up ? op.ul[3] : op.ul[0];
 #pragma unroll
@@ -196,7 +181,7 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
                 if ((sm >> c) & 1u) v.x[c] = cmulx(f, fl, v.x[c]);
             break;
         }
-        case K_TAB: {
+        case RC_TAB: {
             uint32_t g = 0;  // index bits held by the thread's base index
             for (int j = 0; j < op.tw; ++j) g |= ((i0 >> op.tpos[j]) & 1u) << j;
             const float4 *tab = reinterpret_cast<const float4 *>(runs + op.tab_off);
@@ -210,6 +195,7 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
         }
         default: break;
     }
+#undef QS_PAIR_CASES
 }
 
 template <int RB>
@@ -273,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tile_reg(float2 *dst, const flo
             }
             for (int k = R.op_begin; k < R.op_begin + R.op_count; ++k) {
                 const RegOp &op = sops[k];
-                if ((base & op.gmask) != op.gmask) continue;  // uniform over the block
+                if (op.gmask && (base & op.gmask) != op.gmask) continue;  // uniform over the block
                 apply_op<RB>(v, op, i0, R, base, tile, d, runs, ps, nrun);
             }
             if (rd + 1 == d.round_count) {

@@ -12,6 +12,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "cx.cuh"
 #include "qsim_internal.h"
 
@@ -485,6 +487,23 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
                     op.cidx[c] = uint8_t(e);
                 }
             }
+            {  // dispatch code
+                uint32_t all_pairs = 0, all_slots = (1u << (1 << RB)) - 1;
+                if (op.kind == K_DENSE || op.kind == K_RDENSE || op.kind == K_SWAPX)
+                    for (int c = 0; c < (1 << RB); ++c)
+                        if (!((c >> op.k) & 1)) all_pairs |= 1u << c;
+                const int partial = op.smask == all_pairs ? 0 : 4;
+                switch (op.kind) {
+                    case K_DENSE: op.code = uint8_t(RC_DENSE + partial + op.k); break;
+                    case K_RDENSE: op.code = uint8_t(RC_RDENSE + partial + op.k); break;
+                    case K_SWAPX: op.code = uint8_t(RC_SWAP + partial + op.k); break;
+                    case K_PHASE1: op.code = op.smask == all_slots ? RC_PHASE_ALL : RC_PHASE; break;
+                    case K_DIAG: op.code = RC_DIAG; break;
+                    case K_SCALE: op.code = RC_SCALE; break;
+                    case K_TAB: op.code = RC_TAB; break;
+                    default: op.code = RC_PHRUN; break;
+                }
+            }
             regops.push_back(op);
         }
         rounds.push_back(rd);
@@ -591,6 +610,26 @@ int find_swap_runs(const std::vector<Gate> &g, std::vector<int> &run_of, std::ve
     return nrun;
 }
 
+// Shared-memory wavefronts of one warp access (lane byte addresses, `width`
+// bytes each): the largest number of distinct 4-byte words on one bank.
+int wavefronts(const uint32_t *addr, int width) {
+    uint32_t words[32][64];
+    int cnt[32] = {0};
+    int worst = 1;
+    for (int l = 0; l < 32; ++l)
+        for (int w = 0; w < width / 4; ++w) {
+            const uint32_t word = addr[l] / 4 + uint32_t(w);
+            const int bank = int(word & 31);
+            bool seen = false;
+            for (int i = 0; i < cnt[bank]; ++i) seen |= words[bank][i] == word;
+            if (!seen) {
+                words[bank][cnt[bank]++] = word;
+                worst = std::max(worst, cnt[bank]);
+            }
+        }
+    return worst;
+}
+
 // Tile of the permutation pass: the lowest lb qubits (contiguous runs of
 // 2^lb amplitudes) and their images under pi, with lb as large as the shared
 // memory of two tiles allows (at most 12 tile qubits).
@@ -614,6 +653,34 @@ PermDesc perm_desc(const std::vector<int> &pi, int M, qsim_prec prec) {
         }
         for (int j = 0; j < d.ns; ++j) d.spi[j] = sidx[pi[d.spos[j]]];
         for (int j = 0; j < d.nout; ++j) d.opi[j] = oidx[pi[d.opos[j]]];
+        // shared-memory swizzle: fewest wavefronts over the warp writes in index
+        // order and the warp reads at sig(v) (v in index order)
+        const uint32_t n = 1u << d.ns;
+        std::vector<uint32_t> sig(n);
+        for (uint32_t u = 0; u < n; ++u) {
+            uint32_t v = 0;
+            for (int j = 0; j < d.ns; ++j)
+                if ((u >> j) & 1) v |= 1u << d.spi[j];
+            sig[u] = v;
+        }
+        const int ab = int(amp_bytes(prec));
+        long best_cost = -1;
+        for (int sh = 4; sh <= std::max(4, d.ns - 1); ++sh) {
+            long cost = 0;
+            uint32_t wa[32], ra[32];
+            for (uint32_t w0 = 0; w0 < n; w0 += 32) {
+                for (uint32_t l = 0; l < 32; ++l) {
+                    const uint32_t u = (w0 + l) % n, sv = sig[u];
+                    wa[l] = uint32_t(ab) * (u ^ ((u >> sh) & 15u));
+                    ra[l] = uint32_t(ab) * (sv ^ ((sv >> sh) & 15u));
+                }
+                cost += wavefronts(wa, ab) + wavefronts(ra, ab);
+            }
+            if (best_cost < 0 || cost < best_cost) {
+                best_cost = cost;
+                d.sh = sh;
+            }
+        }
         if (perm_smem_bytes(d, prec) <= 96 * 1024) return d;
         best = d;
     }
@@ -754,17 +821,6 @@ int next_event(const qsim_plan *p, cudaStream_t s) {
 }
 
 // --------------------------------------------------------------- fused mode
-float tf32_round(float x) {  // round to nearest (ties away), 10 explicit mantissa bits
-    uint32_t u;
-    std::memcpy(&u, &x, 4);
-    if ((u & 0x7f800000u) != 0x7f800000u) {
-        u += 0x1000u;
-        u &= 0xffffe000u;
-    }
-    std::memcpy(&x, &u, 4);
-    return x;
-}
-
 // Product of the block's gates (in order) as a dense 2^k x 2^k matrix, FP64:
 // each gate's 2x2 operation applied to every column (Section 2.1's pair rule
 // on the 2^k-dimensional block space).
@@ -816,10 +872,19 @@ bool is_unitary(const std::vector<double> &U, int k) {
     return true;
 }
 
-// R_hi and R_lo of the block in the K-major 128-byte-swizzled layout the MMA
-// reads (rows n = output reals, K = input reals, 32 K per 128-byte chunk).
-void block_rimg(const std::vector<double> &U, int k, float *img) {
-    const int n = 1 << k, KR = 2 * n;
+// Shared-memory byte offset of element (row, column c) of a K-major operand
+// with rows of W bytes (W = 128, 64, 32 for k = 5, 4, 3): 16-byte chunks of
+// each row XOR-swizzled by the row bits above them, as the MMA descriptors of
+// layout SW128 / SW64 / SW32 read them.
+uint32_t operand_offset(int W, uint32_t row, uint32_t byte_in_row) {
+    const uint32_t sw = W == 128 ? (row & 7) : (W == 64 ? ((row >> 1) & 3) : ((row >> 2) & 1));
+    return row * uint32_t(W) ^ (sw << 4) ^ byte_in_row;
+}
+
+// R_hi and R_lo (FP16, R scaled by 2^8) of the block as the MMA's B operand:
+// row n = output real, column kk = input real.
+void block_rimg(const std::vector<double> &U, int k, __half *img) {
+    const int n = 1 << k, KR = 2 * n, W = 2 * KR;
     const size_t plane = size_t(KR) * KR;
     for (int r = 0; r < KR; ++r) {
         for (int kk = 0; kk < KR; ++kk) {
@@ -828,10 +893,10 @@ void block_rimg(const std::vector<double> &U, int k, float *img) {
             double v;
             if ((r & 1) == 0) v = (kk & 1) ? -ui : ur;
             else v = (kk & 1) ? ur : ui;
-            const float hi = tf32_round(float(v));
-            const float lo = tf32_round(float(v - double(hi)));
-            const size_t off = size_t(kk >> 5) * (size_t(KR) * 32) + size_t(r >> 3) * 256 + size_t(r & 7) * 32 +
-                               size_t((((kk & 31) >> 2) ^ (r & 7)) << 2) + size_t(kk & 3);
+            v *= 256.0;
+            const __half hi = __float2half_rn(float(v));
+            const __half lo = __float2half_rn(float(v - double(__half2float(hi))));
+            const size_t off = operand_offset(W, uint32_t(r), uint32_t(2 * kk)) / 2;
             img[off] = hi;
             img[plane + off] = lo;
         }
@@ -841,14 +906,15 @@ void block_rimg(const std::vector<double> &U, int k, float *img) {
 FusedDesc fused_desc(int M, int k, const int *bq) {
     FusedDesc d{};
     d.k = k;
+    const int nf = kFusedTileBits - k, NA = 1 << k, NROWS = 1 << nf, KR = 2 * NA, W = 2 * KR;
     uint64_t B = 0;
     for (int j = 0; j < k; ++j) B |= bit(bq[j]);
     uint64_t F = 0;
-    int nf = 0;
-    for (int q = 0; q < M && nf < 7; ++q)
+    int fq[kFusedTileBits], nfq = 0;
+    for (int q = 0; q < M && nfq < nf; ++q)
         if (!(B & bit(q))) {
             F |= bit(q);
-            ++nf;
+            fq[nfq++] = q;
         }
     const uint64_t Uq = B | F;
     int idx[64];
@@ -863,48 +929,88 @@ FusedDesc fused_desc(int M, int k, const int *bq) {
     d.nout = 0;
     for (int q = 0; q < M; ++q)
         if (!(Uq & bit(q))) d.opos[d.nout++] = q;
-    int fq[7], nfq = 0;
-    for (int q = 0; q < M; ++q)
-        if (F & bit(q)) fq[nfq++] = q;
-    for (int a = 0; a < (1 << k); ++a) {
+    for (int a = 0; a < NA; ++a) {
         uint32_t u = 0;
         for (int j = 0; j < k; ++j)
             if ((a >> j) & 1) u |= 1u << idx[bq[j]];
         d.posA[a] = uint16_t(u);
     }
-    for (int m = 0; m < 128; ++m) {
+    for (int m = 0; m < NROWS; ++m) {
         uint32_t u = 0;
-        for (int j = 0; j < 7; ++j)
+        for (int j = 0; j < nf; ++j)
             if ((m >> j) & 1) u |= 1u << idx[fq[j]];
         d.posM[m] = uint16_t(u);
     }
-    int rankB[16], rankF[16];  // u bit -> rank in B / F, or -1
-    for (int i = 0; i < 16; ++i) rankB[i] = rankF[i] = -1;
-    for (int j = 0; j < k; ++j) rankB[idx[bq[j]]] = j;
-    for (int j = 0; j < 7; ++j) rankF[idx[fq[j]]] = j;
-    for (int half = 0; half < 2; ++half)
-        for (int v = 0; v < 64; ++v) {
-            int a = 0, m = 0;
-            for (int i = 0; i < 6; ++i) {
-                if (!((v >> i) & 1)) continue;
-                const int ub = 6 * half + i;
-                if (rankB[ub] >= 0) a |= 1 << rankB[ub];
-                if (rankF[ub] >= 0) m |= 1 << rankF[ub];
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t u = uint32_t(j) << 7;
+        uint64_t off = 0;
+        for (int b = 7; b < kFusedTileBits; ++b)
+            if ((u >> b) & 1) off |= b < d.runbits ? bit(b) : bit(d.rpos[b - d.runbits]);
+        d.runoff2[j] = off;
+    }
+    // split: lane l of split warp w owns sub-vector rows 32 w + l (+ 128 per row
+    // block) and visits combination s ^ skew[l] at step s; pick the skew with the
+    // fewest shared-memory wavefronts over the warp's input reads and operand writes
+    {
+        long best = -1;
+        uint32_t la[32], sa[32];
+        uint8_t g[32];
+        for (int c = 0; c < 18; ++c)
+            for (int sh = 0; sh < 6; ++sh) {
+                for (int l = 0; l < 32; ++l) g[l] = uint8_t(((l * (c == 0 ? 0 : 2 * c - 1)) ^ (sh ? (l >> sh) : 0)) & (NA - 1));
+                long cost = 0;
+                for (int w = 0; w < 4; ++w)
+                    for (int rb = 0; rb < NROWS / 128; ++rb)
+                        for (int st = 0; st < NA; ++st) {
+                            for (int l = 0; l < 32; ++l) {
+                                const int rho = 32 * w + l, a = st ^ g[l];
+                                la[l] = 8u * (uint32_t(d.posA[a]) | d.posM[rb * 128 + rho]);
+                                sa[l] = operand_offset(W, uint32_t(rho), 4u * uint32_t(a));
+                            }
+                            cost += wavefronts(la, 8) + 2 * wavefronts(sa, 4);
+                        }
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    std::memcpy(d.skew, g, 32);
+                }
             }
-            d.decA[half][v] = uint8_t(a);
-            d.decM[half][v] = uint8_t(m);
+    }
+    // epilogue: thread = sub-vector row, writes combination a at swz(posA[a] | posM[m]);
+    // then the tile is read in index order; pick the staging swizzle shift
+    {
+        long best = -1;
+        uint32_t ad[32];
+        for (int r = 4; r <= 8; ++r) {
+            auto swz = [r](uint32_t u) { return u ^ ((u >> r) & 15u); };
+            long cost = 0;
+            for (int w = 0; w < 4; ++w)
+                for (int rb = 0; rb < NROWS / 128; ++rb)
+                    for (int a = 0; a < NA; ++a) {
+                        for (int l = 0; l < 32; ++l) ad[l] = 8u * swz(uint32_t(d.posA[a]) | d.posM[rb * 128 + 32 * w + l]);
+                        cost += wavefronts(ad, 8);
+                    }
+            for (int w = 0; w < 4; ++w)
+                for (int j = 0; j < 32; ++j) {
+                    for (int l = 0; l < 32; ++l) ad[l] = 8u * swz(uint32_t(32 * w + l + 128 * j));
+                    cost += wavefronts(ad, 8);
+                }
+            if (best < 0 || cost < best) {
+                best = cost;
+                d.outsh = r;
+            }
         }
+    }
     return d;
 }
 
 // Greedy grouping into blocks of at most k qubits (every qubit of a gate,
 // controls included, joins the block), padded to exactly k qubits with the
 // lowest free ones.
-void plan_fused(qsim_plan *p, int k, std::vector<float> &rimg) {
+void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
     const int M = p->M;
     std::vector<int> rem(p->gates.size());
     for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
-    const size_t per = fused_rimg_floats(k);
+    const size_t per = fused_rimg_halves(k);
     while (!rem.empty()) {
         uint64_t defN = 0, defA = 0, Q = 0;
         std::vector<int> take, keep;
@@ -930,7 +1036,7 @@ void plan_fused(qsim_plan *p, int k, std::vector<float> &rimg) {
         st.type = S_FUSED;
         st.f = fused_desc(M, k, bq);
         st.rimg = rimg.size();
-        rimg.resize(rimg.size() + per, 0.f);
+        rimg.resize(rimg.size() + per, __float2half_rn(0.f));
         const std::vector<double> U = block_matrix(p->gates, take, bq, k);
         st.f.unitary = is_unitary(U, k) ? 1 : 0;
         block_rimg(U, k, rimg.data() + st.rimg);
@@ -983,7 +1089,7 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
         } else if (st.type == S_PERM) {
             if (int rc = launch_perm(dst, first ? src : dst, p->M, p->prec, st.perm, s)) return rc;
         } else if (st.type == S_FUSED) {
-            if (int rc = launch_fused(dst, first ? src : dst, p->M, st.f, static_cast<const float *>(p->d_rimg) + st.rimg,
+            if (int rc = launch_fused(dst, first ? src : dst, p->M, st.f, static_cast<const __half *>(p->d_rimg) + st.rimg,
                                       p->d_status, s))
                 return rc;
         } else {
@@ -1039,8 +1145,8 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
     int mode = o.mode == QSIM_MODE_AUTO ? QSIM_MODE_TILED : o.mode;
     // The tensor-core kernel runs 4- or 5-qubit blocks of complex64 states
     // with at least 2^(k+7) amplitudes; anything else takes the tile passes.
-    const int k_eff = o.fuse_k == 0 ? 5 : (o.fuse_k <= 4 ? 4 : 5);
-    if (mode == QSIM_MODE_FUSED && (prec != QSIM_C64 || M < k_eff + 7)) mode = QSIM_MODE_TILED;
+    const int k_eff = o.fuse_k == 0 ? 5 : std::max(3, o.fuse_k);
+    if (mode == QSIM_MODE_FUSED && (prec != QSIM_C64 || M < kFusedTileBits)) mode = QSIM_MODE_TILED;
     p->mode = mode;
     {
         int rc = dev_alloc(p, reinterpret_cast<void **>(&p->d_status), sizeof(int));
@@ -1058,10 +1164,10 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
     double bytes = 0;
     if (mode == QSIM_MODE_FUSED) {
         p->fuse_k = k_eff;
-        std::vector<float> rimg;
+        std::vector<__half> rimg;
         plan_fused(p, k_eff, rimg);
         int rc = fused_prepare();
-        if (rc == QSIM_OK) rc = upload(p, &p->d_rimg, rimg.data(), rimg.size() * sizeof(float), &p->rimg_bytes);
+        if (rc == QSIM_OK) rc = upload(p, &p->d_rimg, rimg.data(), rimg.size() * sizeof(__half), &p->rimg_bytes);
         if (rc) {
             plan_release(p);
             return rc;
@@ -1228,7 +1334,10 @@ int qsim_plan_timing(qsim_plan *p, int64_t n_max, double *ms, double *bytes, int
     for (int64_t j = 0; j < n; ++j) {
         if (ms) ms[j] = 0.0;
         if (bytes) bytes[j] = p->steps[j].bytes;
-        if (kind) kind[j] = int32_t(p->steps[j].type);
+        if (kind) {
+            const Step &st = p->steps[j];
+            kind[j] = st.type == S_TILE && st.d.round_count > 0 ? 4 : int32_t(st.type);
+        }
     }
     if (p->ev_used > 0) {
         QS_CUDA(cudaEventSynchronize(p->ev_pool[p->ev_used - 1]));

@@ -156,7 +156,21 @@ struct RegOp {
     uint32_t nmask;      // tile bits outside the slots that the thread's index must have set
     uint32_t tbn;        // K_DIAG: target bit when it is not a slot qubit (tested on the thread's index)
     uint16_t tsel;       // K_DIAG: slots whose target bit is set (target a slot qubit)
-    uint16_t pad2[3];
+    uint8_t code;        // dispatch code of the register kernel (RegCode)
+    uint8_t pad3;
+    uint16_t pad2[2];
+};
+// Dispatch code of a RegOp: pair kinds by (kind, every pair touched, slot bit k).
+enum RegCode : uint8_t {
+    RC_DENSE = 0,     // + 4 * partial + k
+    RC_RDENSE = 8,    // + 4 * partial + k
+    RC_SWAP = 16,     // + 4 * partial + k
+    RC_PHASE_ALL = 24,
+    RC_PHASE = 25,
+    RC_DIAG = 26,
+    RC_SCALE = 27,
+    RC_TAB = 28,
+    RC_PHRUN = 29,
 };
 static_assert(sizeof(RegOp) % 16 == 0, "RegOp is copied in 16-byte units");
 struct RoundDesc {
@@ -175,22 +189,28 @@ int tile_prepare(qsim_prec prec);  // one-time kernel attributes (call before an
 // Geometry of one fused k-qubit block over a state of M qubits (see
 // k_fused_tc.cu): tile qubits U = B u F (B the block, F the 7 lowest other
 // qubits), tile-local index u = bits of U in ascending order.
+// Fused tensor-core pass: tiles of 2^kFusedTileBits amplitudes, the k block
+// qubits plus the 12 - k lowest other qubits; at most 2^kFusedRowBits
+// sub-vectors per tile.
+constexpr int kFusedTileBits = 12;
+constexpr int kFusedRowBits = 9;
 struct FusedDesc {
     int k;
     int unitary;                 // the block is unitary: rescale each sub-vector to its input norm
-    int runbits;                 // qubits 0..runbits-1 are all in U: runs of 2^runbits amplitudes
-    int nrb;                     // qubits of U above the run: k + 7 - runbits
-    int rpos[12];                // their global positions, ascending
-    int nout;                    // qubits outside U (number the tiles)
+    int runbits;                 // qubits 0..runbits-1 are all in the tile: runs of 2^runbits amplitudes
+    int nrb;                     // tile qubits above the run: 12 - runbits
+    int rpos[kFusedTileBits];    // their device positions, ascending
+    int nout;                    // qubits outside the tile (number the tiles)
     int opos[QSIM_MAX_QUBITS];
+    int outsh;                   // staging swizzle: bits [0,4) of the tile index ^= bits [outsh, outsh+4)
     uint16_t posA[32];           // u of block combination a (sub-vector 0)
-    uint16_t posM[128];          // u of sub-vector m (combination 0)
-    uint8_t decA[2][64];         // a from u: decA[0][u & 63] | decA[1][u >> 6]
-    uint8_t decM[2][64];         // m from u, likewise
+    uint16_t posM[1 << kFusedRowBits];  // u of sub-vector m (combination 0)
+    uint8_t skew[32];            // split: lane l visits combination s ^ skew[l] at step s
+    uint64_t runoff2[32];        // device offset of tile index 128 j (tile 0)
 };
 int fused_prepare();
-size_t fused_rimg_floats(int k);  // floats of one block's R_hi + R_lo image
-int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const float *rimg_dev, int *status,
+size_t fused_rimg_halves(int k);  // FP16 values of one block's R_hi + R_lo image
+int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const void *rimg_dev, int *status,
                  cudaStream_t s);
 
 // ------------------------------------------------------- qubit permutation
@@ -200,6 +220,7 @@ int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const fl
 // ascending and opi[j] = outside index of pi(opos[j]).
 struct PermDesc {
     int ns, nout, lb;  // tile qubits, outside qubits, low qubits per contiguous run
+    int sh;            // shared-memory swizzle: bits [0,4) of the local index ^= bits [sh, sh+4)
     int spos[12], spi[12];
     int opos[QSIM_MAX_QUBITS], opi[QSIM_MAX_QUBITS];
 };

@@ -296,18 +296,18 @@ def _fused_case(orc, M, recs, k, x=None):
     return plan
 
 
-@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("k", [3, 4, 5])
 @pytest.mark.parametrize("M", [12, 13, 16, 20])
 def test_fused_random_circuits(orc, k, M):
-    """Dense k-qubit blocks on the tensor cores (split TF32, FP32 accumulation)."""
-    if M < k + 7:
-        pytest.skip("state smaller than one fused tile")
+    """Dense k-qubit blocks on the tensor cores (split FP16 with a power-of-two
+    scale per sub-vector, FP32 accumulation); M = 12 is one tile."""
     rng = np.random.default_rng(300 + 7 * M + k)
     _fused_case(orc, M, _rand_gates(rng, M, 120), k)
 
 
-@pytest.mark.parametrize("k", [4, 5])
-@pytest.mark.parametrize("qubits", [(0, 1, 2, 3, 4), (12, 13, 14, 15, 16), (0, 3, 7, 11, 16), (1, 2, 9, 10, 15)])
+@pytest.mark.parametrize("k", [3, 4, 5])
+@pytest.mark.parametrize("qubits", [(0, 1, 2, 3, 4), (12, 13, 14, 15, 16), (0, 3, 7, 11, 16), (1, 2, 9, 10, 15),
+                                    (5, 6, 7, 8, 9), (4, 11, 12, 13, 14)])
 def test_fused_block_positions(orc, k, qubits):
     """One block on low, high and mixed qubit positions (tile layouts differ)."""
     M = 17
@@ -324,7 +324,7 @@ def test_fused_block_positions(orc, k, qubits):
     assert plan.stats()["n_blocks"] == 1
 
 
-@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("k", [3, 4, 5])
 def test_fused_qft_and_brickwork(orc, k):
     M = 18
     c = W.circuit_c2_qft(M, sigma=1e-4)
@@ -344,6 +344,34 @@ def test_fused_qft_and_brickwork(orc, k):
     assert abs(F - Fo) <= TOL64_F and abs(nrm - nrmo) <= TOL64_F
     b = W.circuit_c4_brickwork_toffoli(M, layers=8)
     _fused_case(orc, M, b["noisy"], k, x)
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_fused_dynamic_range(orc, k):
+    """Groups of 32 amplitudes whose magnitudes span 50 decades, a fifth of them
+    zero, under gates on qubits 0..2 (each sub-vector stays inside its group):
+    every sub-vector is scaled on its own before the FP16 split, so each group
+    keeps its relative precision, and zero groups stay exactly zero."""
+    M = 14
+    rng = np.random.default_rng(93 + k)
+    x = W.random_state(M, seed=5).astype(np.complex128).reshape(-1, 32)
+    mag = 10.0 ** rng.uniform(-25, 25, size=x.shape[0])
+    mag[rng.random(mag.size) < 0.2] = 0.0
+    x = (x * mag[:, None]).astype(np.complex64).reshape(-1)
+    recs = _rand_gates(rng, 3, 40)
+    plan = qs.Plan(M, recs, mode="fused", fuse_k=k)
+    st = qs.State(M).set(x)
+    plan.execute(st)
+    plan.status()
+    assert plan.stats()["mode"] == qs.MODE_FUSED
+    got = st.get().astype(np.complex128).reshape(-1, 32)
+    ref = orc.run(M, recs, x.astype(np.complex128), nthreads=NT).reshape(-1, 32)
+    assert np.all(np.isfinite(got))
+    zero = mag == 0.0
+    assert np.all(got[zero] == 0)
+    gmax = np.abs(ref[~zero]).max(axis=1)
+    err = np.abs(got[~zero] - ref[~zero]).max(axis=1) / gmax
+    assert err.max() <= 2e-6, err.max()
 
 
 def test_fused_non_unitary_block(orc):
