@@ -38,6 +38,10 @@ WORKLOADS = {
     "qft-m28-c64": dict(M=28, sigma=1e-4),
     # smaller case of the same circuit for ncu captures (512 MiB per state, > L2)
     "qft-m26-c64": dict(M=26, sigma=1e-4),
+    # 33-qubit brickwork (24 layers, Haar SU(2) + CNOT, Toffoli every 4th layer,
+    # over-rotation sigma=1e-3), both states resident (128 GiB): tiled, fused and
+    # one-gate-per-launch forms compared (run on its own: minutes per mode)
+    "brickwork-m33-c64": dict(M=33, sigma=1e-3),
 }
 
 
@@ -535,6 +539,83 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def run_brickwork(args, rank, world, local):
+    """The M=33 brickwork from |0...0>: per mode, one step = reset both states,
+    the error-free and the noisy circuit in place, fidelity and norm read back."""
+    import torch
+
+    import paper_quant_ph_9804039_gb300 as qs
+    from workloads import generators as W
+
+    wl = WORKLOADS[args.workload]
+    M = wl["M"]
+    c = W.circuit_c4_brickwork_toffoli(M, layers=24, sigma=wl["sigma"])
+    n = len(c["ideal"])
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    ideal = qs.State(M, device=dev, stream=stream)
+    noisy = qs.State(M, device=dev, stream=stream)
+    peak, peak_src = measured_peaks()
+    modes = {}
+    for mode, steps, warm in (("tiled", max(1, args.steps), max(1, min(args.warmup, 2))),
+                              ("fused", max(1, args.steps), max(1, min(args.warmup, 2))),
+                              ("unfused", 1, 0)):
+        if mode == "unfused" and args.no_unfused:
+            continue
+        p_i = qs.Plan(M, c["ideal"], mode=mode)
+        p_n = qs.Plan(M, c["noisy"], mode=mode)
+
+        def step():
+            ideal.reset()
+            noisy.reset()
+            p_i.execute(ideal)
+            p_n.execute(noisy)
+            return qs.fidelity(ideal, noisy)
+
+        for _ in range(warm):
+            step()
+        torch.cuda.synchronize()
+        p_i.set_timing(True)
+        p_n.set_timing(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                F, nrm = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+        tot_ms = tot_bytes = 0.0
+        for p in (p_i, p_n):
+            t_ms, t_bytes, _, execs = p.timing()
+            tot_ms += sum(t_ms)
+            tot_bytes += sum(t_bytes) * execs
+        st = p_n.stats()
+        gbs = tot_bytes / (tot_ms / 1e3) / 1e9
+        modes[mode] = {"amp_updates_per_s": job_throughput(2.0 * n * float(1 << M), world, ms), "ms_per_step": ms,
+                       "steps": steps, "warmup": warm, "passes_per_circuit": st["n_passes"],
+                       "launch_GB/s": round(gbs, 1), "launch_frac_of_measured_hbm": round(gbs / peak, 4),
+                       "F": F, "norm": nrm, "clocks": clk.summary()}
+        p_i.set_timing(False)
+        p_n.set_timing(False)
+        del p_i, p_n
+    best = max(modes, key=lambda m: modes[m]["amp_updates_per_s"])
+    if rank == 0:
+        print(json.dumps({
+            "metric": "amplitude-updates/s", "value": modes[best]["amp_updates_per_s"], "unit": "amp-updates/s",
+            "n_gpus": world, "steps": modes[best]["steps"], "warmup": modes[best]["warmup"],
+            "ms_per_step": modes[best]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+            "config": {"workload": args.workload, "M": M, "circuit": "brickwork+toffoli", "layers": 24,
+                       "sigma": wl["sigma"], "gates_per_circuit": n, "circuits_per_step": 2, "input": "|0...0>",
+                       "best_mode": best, "l2": "inputs larger than L2 (64 GiB per state)",
+                       "parallelism": f"replicas{world}"},
+            "modes": modes, "peak_GB/s": peak, "peak_source": peak_src}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup()
@@ -542,7 +623,10 @@ def main():
         run_reference(args, rank, world)
         return
     dist_init(world, local)
-    run_ours(args, rank, world, local)
+    if args.workload.startswith("brickwork"):
+        run_brickwork(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

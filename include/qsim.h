@@ -172,6 +172,13 @@ int qsim_plan_execute(const qsim_plan *plan, qsim_state *dst, const qsim_state *
 
 int qsim_plan_stats_get(const qsim_plan *plan, qsim_plan_stats *out);
 
+/* A text description of the plan's passes (outside the paper; for tests and
+ * tuning): one line per pass (kind, tile qubits, op and round counts) and,
+ * for register tile passes, one line per round (slot qubits, each op's kind).
+ * Writes at most len - 1 characters and a terminating NUL into buf (buf may be
+ * NULL when len is 0); *needed (may be NULL) = the full length + 1. */
+int qsim_plan_describe(const qsim_plan *plan, char *buf, int64_t len, int64_t *needed);
+
 /* Wait for the device and report whether any kernel of this plan gave up a
  * bounded wait since the last call: QSIM_OK, or QSIM_ETIMEOUT (the affected
  * state is then undefined).  Clears the record. */

@@ -104,6 +104,7 @@ SIGNATURES = [
                                         ctypes.POINTER(_vp)]),
     ("qsim_plan_execute", ctypes.c_int, [_vp, _vp, _vp]),
     ("qsim_plan_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(PlanStats)]),
+    ("qsim_plan_describe", ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     ("qsim_plan_status", ctypes.c_int, [_vp]),
     ("qsim_plan_destroy", None, [_vp]),
     ("qsim_plan_set_timing", ctypes.c_int, [_vp, ctypes.c_int]),
@@ -326,6 +327,14 @@ class Plan:
         s = PlanStats()
         _check(_lib.qsim_plan_stats_get(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+    def describe(self) -> str:
+        """Text description of the passes, rounds and op kinds."""
+        n = ctypes.c_int64(0)
+        _check(_lib.qsim_plan_describe(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(int(n.value))
+        _check(_lib.qsim_plan_describe(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.value.decode()
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -31,11 +31,15 @@
 // set of contiguous runs of >= 128 amplitudes, loaded by bulk TMA copies
 // (cp.async.bulk).  Sub-vector m (0 .. 2^(12-k) - 1) and block combination a
 // sit at u = posA[a] | posM[m]; the 2^(12-k) sub-vectors form 2^(5-k) MMA
-// row blocks of 128.
+// row blocks of 128.  A tile is loaded in 16-byte asynchronous copies
+// (cp.async) by all lanes of the producer warp: bulk copies of the 1 KiB runs
+// of a tile on high qubits were measured at half the bandwidth.
 //
 // Per CTA (persistent over tiles, one per SM, 320 threads), warp-specialised
 // and pipelined over tiles:
-//   warp 0       producer: bulk copies of a tile into one of 3 input stages;
+//   warp 0       producer: asynchronous copies of a tile into one of 3 input
+//                stages, each lane arriving on the stage's mbarrier when its
+//                copies have landed;
 //   warp 1       MMA: 12 tcgen05.mma per tile (3 products x row blocks x
 //                K steps of 16) into one of 2 TMEM accumulators (64 columns
 //                each), committed to mbarriers;
@@ -48,7 +52,7 @@
 //                (tcgen05.ld), removes the scale, renormalises, writes the
 //                amplitudes into an XOR-swizzled staging tile, and the four
 //                warps then copy the staging tile to device memory in
-//                coalesced runs.
+//                coalesced runs (8 loads in flight per thread).
 // Every mbarrier wait is bounded (2 s of globaltimer); on a timeout the CTA
 // records QSIM_ETIMEOUT in the status word, the other roles leave their loops,
 // the producer waits (bounded) for its copies in flight, the MMA warp for its
@@ -122,6 +126,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// arrive on bar once this thread's earlier cp.async copies have landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -221,7 +233,8 @@ struct SmemCtl {
     uint64_t full_acc[kNA], empty_acc[kNA];
     uint64_t bar_r;
     uint64_t epi_full, epi_free;          // staging tile written / copied out (4 epilogue warps)
-    uint64_t gofs[32];                    // device offset of tile-local index 128 j, this tile (epilogue)
+    uint64_t runoff[32];                  // device offset of run r of a tile (tile 0)
+    uint64_t runoff2[32];                 // device offset of tile-local index 128 j (tile 0)
     uint32_t tmem;
     int abort;
     uint32_t swA8[32];                    // 8 * swz(posA[a]): staging byte offset of combination a
@@ -237,8 +250,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_fused_tc(float2 *dst, const float2 *src, FusedDesc d, const __half *__restrict__ rimg, uint64_t ntiles,
                int *status) {
     using C = Cfg<KF>;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // 1024-byte aligned, derived from the shared array by pointer arithmetic so
+    // that every access through it stays a shared-memory access (no aliasing
+    // with device memory for the compiler to assume)
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ SmemCtl ctl;
     volatile int *abort = &ctl.abort;
 
@@ -247,9 +263,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t run_amps = 1u << d.runbits;
     for (int m = tid; m < C::NROWS; m += kThreads) ctl.posM[m] = d.posM[m];
     if (tid < C::NA) ctl.swA8[tid] = 8u * stg_swz(d.posA[tid], d.outsh);
+    if (tid < 32) ctl.runoff2[tid] = d.runoff2[tid];
+    if (tid < nrun) {
+        uint64_t off = 0;
+        for (int b = 0; b < d.nrb; ++b)
+            if ((tid >> b) & 1) off |= uint64_t(1) << d.rpos[b];
+        ctl.runoff[tid] = off;
+    }
     if (tid == 0) {
         for (int b = 0; b < kNIn; ++b) {
-            mbar_init(&ctl.full_in[b], 1);
+            mbar_init(&ctl.full_in[b], 32);
             mbar_init(&ctl.empty_in[b], 4);
         }
         for (int b = 0; b < kNA; ++b) {
@@ -270,17 +293,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = ctl.tmem;
     const uint64_t n_local = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    // device offset of the CTA's i-th tile: lane j contributes outside bit j (a
+    // warp OR-reduction, every lane of the warp calls it)
+    const int my_opos = lane < d.nout ? d.opos[lane] : 0;
     auto tile_base = [&](uint64_t i) {
         const uint64_t tile = blockIdx.x + i * gridDim.x;
-        uint64_t base = 0;
-        for (int j = 0; j < d.nout; ++j)
-            if ((tile >> j) & 1) base |= uint64_t(1) << d.opos[j];
-        return base;
+        const uint64_t mine = (lane < d.nout && ((tile >> lane) & 1)) ? uint64_t(1) << my_opos : 0;
+        const uint32_t lo = __reduce_or_sync(0xffffffffu, uint32_t(mine));
+        const uint32_t hi = __reduce_or_sync(0xffffffffu, uint32_t(mine >> 32));
+        return (uint64_t(hi) << 32) | lo;
     };
     bool ok = true;
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
+        // all 32 lanes copy the tile in 16-byte pieces (cp.async), each lane
+        // arriving on the stage's barrier once its copies have landed
         uint64_t issued = 0;
         if (lane == 0) {
             unsigned char *Bs = sm + C::OFF_B;
@@ -288,40 +316,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_expect_tx(&ctl.bar_r, 2 * C::B_BYTES);
             bulk_g2s(Bs, rimg, C::B_BYTES, &ctl.bar_r);
             bulk_g2s(Bs + bstride, rimg + C::B_BYTES / 2, C::B_BYTES, &ctl.bar_r);
-            for (uint64_t i = 0; i < n_local; ++i) {
-                const int s = int(i % kNIn);
-                if (i >= kNIn && !mbar_wait(&ctl.empty_in[s], uint32_t(((i / kNIn) & 1) ^ 1), abort)) {
-                    ok = false;
-                    break;
-                }
-                const uint64_t base = tile_base(i);
-                float2 *buf = reinterpret_cast<float2 *>(sm + C::OFF_IN + size_t(s) * kInBytes);
-                mbar_expect_tx(&ctl.full_in[s], kInBytes);
-                for (int r = 0; r < nrun; ++r) {
-                    uint64_t off = 0;
-                    for (int b = 0; b < d.nrb; ++b)
-                        if ((r >> b) & 1) off |= uint64_t(1) << d.rpos[b];
-                    bulk_g2s(buf + size_t(r) * run_amps, src + base + off, run_amps * 8, &ctl.full_in[s]);
-                }
-                issued = i + 1;
-            }
-            if (!ok) {
-                atomicExch(status, QSIM_ETIMEOUT);
-                ctl.abort = 1;
-            }
-            // the copies of the last stages may still be landing if a consumer left early
-            const uint64_t first = issued > kNIn ? issued - kNIn : 0;
-            for (uint64_t j = first; j < issued; ++j) {
-                const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(&ctl.full_in[j % kNIn], uint32_t((j / kNIn) & 1)))
-                    if (globaltimer() - t0 > kWaitNs) break;
-            }
-            {
-                const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(&ctl.bar_r, 0))
-                    if (globaltimer() - t0 > kWaitNs) break;
-            }
         }
+        const uint32_t rmask = run_amps - 1;
+        for (uint64_t i = 0; i < n_local; ++i) {
+            const int s = int(i % kNIn);
+            if (i >= kNIn && !warp_wait(&ctl.empty_in[s], uint32_t(((i / kNIn) & 1) ^ 1), abort)) {
+                ok = false;
+                break;
+            }
+            const uint64_t base = tile_base(i);
+            unsigned char *buf = sm + C::OFF_IN + size_t(s) * kInBytes;
+#pragma unroll 8
+            for (int c = 0; c < kTileAmps / 2 / 32; ++c) {
+                const uint32_t u = 2u * (uint32_t(c) * 32u + uint32_t(lane));
+                cp_async16(buf + 8u * u, src + base + ctl.runoff[u >> d.runbits] + (u & rmask));
+            }
+            cp_async_arrive(&ctl.full_in[s]);
+            issued = i + 1;
+        }
+        cp_async_wait_all();
+        if (!ok) {
+            if (lane == 0) atomicExch(status, QSIM_ETIMEOUT);
+            ctl.abort = 1;
+        }
+        if (lane == 0) {
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try_wait(&ctl.bar_r, 0))
+                if (globaltimer() - t0 > kWaitNs) break;
+        }
+        (void)issued;
         __syncwarp();
     } else if (warp == 1) {
         // ----------------------------------------------------------------- MMA
@@ -483,10 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = false;
                 break;
             }
-            if (warp == 6) {
-                const uint64_t base = tile_base(i);
-                ctl.gofs[lane] = base | d.runoff2[lane];
-            }
+            const uint64_t base = tile_base(i);
 #pragma unroll
             for (int rb = 0; rb < C::NRB; ++rb) {
                 const uint32_t swm = 8u * stg_swz(ctl.posM[rb * 128 + rho], d.outsh);
@@ -502,12 +522,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             const uint32_t swt = stg_swz(uint32_t(te), d.outsh);
-#pragma unroll 8
-            for (int j = 0; j < 32; ++j) {
-                // u = te + 128 j; staging index swz(u) = swz(te) ^ swz(128 j)
-                const uint32_t su = swt ^ stg_swz(uint32_t(j) << 7, d.outsh);
-                const float2 v = *reinterpret_cast<const float2 *>(outb + 8u * su);
-                dst[ctl.gofs[j] + uint32_t(te)] = v;
+            float2 *dbase = dst + base + uint32_t(te);
+#pragma unroll
+            for (int j0 = 0; j0 < 32; j0 += 8) {  // 8 loads in flight, then their stores
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)  // u = te + 128 j; staging index swz(u) = swz(te) ^ swz(128 j)
+                    v[j] = *reinterpret_cast<const float2 *>(outb + 8u * (swt ^ stg_swz(uint32_t(j0 + j) << 7, d.outsh)));
+#pragma unroll
+                for (int j = 0; j < 8; ++j) dbase[ctl.runoff2[j0 + j]] = v[j];
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl.epi_free);

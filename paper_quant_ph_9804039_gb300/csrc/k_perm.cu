@@ -20,6 +20,7 @@ namespace qs {
 namespace {
 
 constexpr int kPermThreads = 256;
+constexpr int kBatch = 8;  // global loads per thread in flight
 
 // The first lb tile qubits are qubits 0..lb-1, so a local index u sits at
 // offset (u & (2^lb - 1)) | hoff[u >> lb] of the vector; sig(u) (the local
@@ -65,12 +66,28 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(T2 *dst, const T2 *src
                 base2 |= uint64_t(1) << d.opos[d.opi[j]];
             }
         if (o2 < o) continue;  // the partner's block does this pair
+        // loads in batches of kBatch per thread, all in flight before the
+        // shared-memory stores that consume them
         if (o2 != o) {
-            for (uint32_t u = threadIdx.x; u < n; u += blockDim.x) {
-                const uint64_t off = (u & lmask) | hoff[u >> lb];
-                const T2 x = src[base | off], y = src[base2 | off];
-                A[pad(u)] = x;
-                B[pad(u)] = y;
+            for (uint32_t u0 = threadIdx.x; u0 < n; u0 += kBatch * kPermThreads) {
+                T2 x[kBatch], y[kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const uint32_t u = u0 + uint32_t(j) * kPermThreads;
+                    if (u < n) {
+                        const uint64_t off = (u & lmask) | hoff[u >> lb];
+                        x[j] = src[base | off];
+                        y[j] = src[base2 | off];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const uint32_t u = u0 + uint32_t(j) * kPermThreads;
+                    if (u < n) {
+                        A[pad(u)] = x[j];
+                        B[pad(u)] = y[j];
+                    }
+                }
             }
             __syncthreads();
             // tile o lands on tile o2: out[base2 | off(v)] = A[sig^-1(v)] = A[sig(v)]
@@ -81,8 +98,19 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(T2 *dst, const T2 *src
                 dst[base | off] = B[ps];
             }
         } else {
-            for (uint32_t u = threadIdx.x; u < n; u += blockDim.x)
-                A[pad(u)] = src[base | (u & lmask) | hoff[u >> lb]];
+            for (uint32_t u0 = threadIdx.x; u0 < n; u0 += kBatch * kPermThreads) {
+                T2 x[kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const uint32_t u = u0 + uint32_t(j) * kPermThreads;
+                    if (u < n) x[j] = src[base | (u & lmask) | hoff[u >> lb]];
+                }
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const uint32_t u = u0 + uint32_t(j) * kPermThreads;
+                    if (u < n) A[pad(u)] = x[j];
+                }
+            }
             __syncthreads();
             for (uint32_t v = threadIdx.x; v < n; v += blockDim.x)
                 dst[base | (v & lmask) | hoff[v >> lb]] = A[pad(slo[v & lmask] | shi[v >> lb])];

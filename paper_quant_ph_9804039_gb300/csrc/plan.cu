@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -53,6 +54,8 @@ struct qsim_plan {
     size_t regops_bytes = 0;
     void *d_rounds = nullptr;
     size_t rounds_bytes = 0;
+    std::vector<RegOp> h_regops;  // host copies, for qsim_plan_describe
+    std::vector<RoundDesc> h_rounds;
     int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
     int fuse_k = 0;
     // non-null: device tables are allocated and freed stream-ordered on this
@@ -1229,6 +1232,8 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
                 rc = upload(p, &p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
                 if (rc == QSIM_OK) rc = upload(p, &p->d_regops, regops.data(), regops.size() * sizeof(RegOp), &p->regops_bytes);
                 if (rc == QSIM_OK) rc = upload(p, &p->d_rounds, rounds.data(), rounds.size() * sizeof(RoundDesc), &p->rounds_bytes);
+                p->h_regops = std::move(regops);
+                p->h_rounds = std::move(rounds);
             } else {
                 std::vector<TileOp<double2>> ops;
                 for (size_t si = 0; si < segs.size(); ++si) {
@@ -1353,6 +1358,61 @@ int qsim_plan_timing(qsim_plan *p, int64_t n_max, double *ms, double *bytes, int
     if (executions) *executions = p->timed_execs;
     p->ev_used = 0;
     p->timed_execs = 0;
+    return QSIM_OK;
+}
+
+int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *needed) {
+    if (!p) { set_error("plan is NULL"); return QSIM_EINVAL; }
+    if (len > 0 && !buf) { set_error("buf is NULL"); return QSIM_EINVAL; }
+    std::string out;
+    char line[512];
+    auto add = [&](const char *fmt, auto... args) {
+        std::snprintf(line, sizeof line, fmt, args...);
+        out += line;
+    };
+    static const char *kinds[] = {"DENSE", "RDENSE", "SWAP"};
+    add("M=%d prec=%s mode=%d steps=%zu\n", p->M, p->prec == QSIM_C64 ? "c64" : "c128", p->mode, p->steps.size());
+    for (size_t j = 0; j < p->steps.size(); ++j) {
+        const Step &st = p->steps[j];
+        if (st.type == S_GATE) {
+            add("step %zu GATE t=%d nc=%d kind=%d\n", j, st.g.t, st.g.nc, int(st.g.kind));
+        } else if (st.type == S_PERM) {
+            add("step %zu PERM tile_qubits=%d low=%d\n", j, st.perm.ns, st.perm.lb);
+        } else if (st.type == S_FUSED) {
+            add("step %zu FUSED k=%d unitary=%d runbits=%d qubits=", j, st.f.k, st.f.unitary, st.f.runbits);
+            for (int a = 0; a < st.f.k; ++a) add("%d ", __builtin_ctz(st.f.posA[1 << a]));
+            add("(tile positions)\n");
+        } else {
+            add("step %zu TILE b=%d L=%d high=", j, st.d.b, st.d.L);
+            for (int h = 0; h < st.d.nh; ++h) add("%d%s", st.d.hpos[h], h + 1 < st.d.nh ? "," : "");
+            add(" ops=%d rounds=%d\n", st.d.op_count, st.d.round_count);
+            for (int r = 0; r < st.d.round_count; ++r) {
+                const RoundDesc &rd = p->h_rounds[size_t(st.d.round_begin + r)];
+                const int RB = st.d.b - kRegThreadBits;
+                add("  round %d slots=", r);
+                for (int k = 0; k < RB; ++k) add("%d%s", rd.pos[k], k + 1 < RB ? "," : "");
+                add(" ops:");
+                for (int k = 0; k < rd.op_count; ++k) {
+                    const RegOp &op = p->h_regops[size_t(st.d.op_begin + rd.op_begin + k)];
+                    const int c = op.code;
+                    if (c < RC_PHASE_ALL) add(" %s%s/%d", kinds[c / 8], (c & 4) ? "p" : "", c & 3);
+                    else if (c == RC_PHASE_ALL || c == RC_PHASE) add(" PHASE");
+                    else if (c == RC_DIAG) add(" DIAG");
+                    else if (c == RC_SCALE) add(" SCALE");
+                    else if (c == RC_TAB) add(" TAB%d", op.tw);
+                    else add(" PHRUN");
+                    if (op.gmask) add("g");
+                }
+                add("\n");
+            }
+        }
+    }
+    if (needed) *needed = int64_t(out.size()) + 1;
+    if (len > 0) {
+        const size_t n = std::min(out.size(), size_t(len - 1));
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
     return QSIM_OK;
 }
 

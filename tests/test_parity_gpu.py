@@ -168,6 +168,32 @@ def test_phase_runs(orc, prec, M, tile_bits):
     _close(st.get(), orc.run(M, recs, x128, nthreads=NT), prec)
 
 
+@pytest.mark.parametrize("M,tile_bits", [(14, 12), (18, 12), (18, 11), (22, 12)])
+def test_phase_runs_one_shared_qubit(orc, M, tile_bits):
+    """Runs whose controlled phases all share one qubit q (the quantum FFT's
+    ladder after a Hadamard), with q as target or as control, controls inside
+    and outside the tile, and single-qubit phases on other qubits mixed in."""
+    rng = np.random.default_rng(70 + M + tile_bits)
+    recs = []
+    for layer in range(6):
+        q = int(rng.integers(M))
+        recs.append(W.gate_record(W.mat_h(), q))
+        for _ in range(25):
+            o = int(rng.choice([v for v in range(M) if v != q]))
+            r = rng.random()
+            if r < 0.6:
+                recs.append(W.gate_record(W.mat_phase(float(rng.uniform(-7, 7))), q, (o,)))
+            elif r < 0.8:
+                recs.append(W.gate_record(W.mat_phase(float(rng.uniform(-7, 7))), o, (q,)))
+            else:
+                recs.append(W.gate_record(np.diag(np.exp(1j * rng.uniform(-7, 7, 2))), o))
+        recs.append(W.gate_record(W.mat_haar_su2(rng), int(rng.integers(M))))
+    recs = W._pack(recs)
+    x, x128 = _input(M, "c64")
+    st = qs.State(M, "c64").set(x).apply_circuit(recs, mode="tiled", tile_bits=tile_bits)
+    _close(st.get(), orc.run(M, recs, x128, nthreads=NT), "c64")
+
+
 @pytest.mark.parametrize("M", [14, 18])
 def test_brickwork_toffoli_complex64(orc, M):
     """The brickwork + Toffoli workload at reduced M, tiled and unfused."""
