@@ -103,6 +103,19 @@ __device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op) {
     }
 }
 
+// Hadamard without its factor: (a, b) <- (a + b, a - b) on slot bit K.
+template <int RB, int K>
+__device__ __forceinline__ void pairs_had(Slots<RB> &v) {
+#pragma unroll
+    for (int c = 0; c < (1 << RB); ++c) {
+        if (c & (1 << K)) continue;
+        const int c1 = c | (1 << K);
+        const float2 a = v.x[c], b = v.x[c1];
+        v.x[c] = make_float2(a.x + b.x, a.y + b.y);
+        v.x[c1] = make_float2(a.x - b.x, a.y - b.y);
+    }
+}
+
 template <int RB>
 __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t i0, const RoundDesc &R,
                                          uint64_t base, uint64_t tile, const TilePassDesc &d,
@@ -152,6 +165,10 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
         QS_PAIR_CASES(RC_DENSE, false, false)
         QS_PAIR_CASES(RC_RDENSE, false, true)
         QS_PAIR_CASES(RC_SWAP, true, false)
+        case RC_HAD + 0: pairs_had<RB, 0>(v); break;
+        case RC_HAD + 1: pairs_had<RB, 1>(v); break;
+        case RC_HAD + 2: pairs_had<RB, 2>(v); break;
+        case RC_HAD + 3: if constexpr (RB > 3) pairs_had<RB, 3>(v); break;
         case RC_PHASE_ALL: {
 #pragma unroll
             for (int c = 0; c < S; ++c) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
@@ -263,6 +280,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_tile_reg(float2 *dst, const flo
                 apply_op<RB>(v, op, i0, R, base, tile, d, runs, ps, nrun);
             }
             if (rd + 1 == d.round_count) {
+                if (d.pscale_on) {  // the pass's deferred Hadamard factors, compensated
+#pragma unroll
+                    for (int c = 0; c < S; ++c)
+                        v.x[c] = make_float2(fmaf(v.x[c].x, d.pscale_hi, v.x[c].x * d.pscale_lo),
+                                             fmaf(v.x[c].y, d.pscale_hi, v.x[c].y * d.pscale_lo));
+                }
 #pragma unroll
                 for (int c = 0; c < S; ++c) {
                     const uint32_t i = i0 | dep[c];

@@ -370,6 +370,8 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
     if (int(items.size()) > kMaxRegOpsPerPass) return false;
     d.round_begin = int(rounds.size());
     d.op_begin = int(regops.size());
+    double pscale = 1.0;  // product of the deferred Hadamard factors
+    int nhad = 0;
     std::vector<int> rem(items.size());
     for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
     bool first = true;
@@ -496,9 +498,18 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
                     for (int c = 0; c < (1 << RB); ++c)
                         if (!((c >> op.k) & 1)) all_pairs |= 1u << c;
                 const int partial = op.smask == all_pairs ? 0 : 4;
+                // (at most 64 per pass: amplitudes grow by up to sqrt(2) per deferred factor)
+                const bool had = op.kind == K_RDENSE && partial == 0 && op.nmask == 0 && op.gmask == 0 && nhad < 64 &&
+                                 op.u[0].x > 0.f && op.u[1].x == op.u[0].x && op.u[2].x == op.u[0].x &&
+                                 op.u[3].x == -op.u[0].x && op.ul[1].x == op.ul[0].x && op.ul[2].x == op.ul[0].x &&
+                                 op.ul[3].x == -op.ul[0].x;
+                if (had) {
+                    pscale *= double(op.u[0].x) + double(op.ul[0].x);
+                    ++nhad;
+                }
                 switch (op.kind) {
                     case K_DENSE: op.code = uint8_t(RC_DENSE + partial + op.k); break;
-                    case K_RDENSE: op.code = uint8_t(RC_RDENSE + partial + op.k); break;
+                    case K_RDENSE: op.code = uint8_t((had ? RC_HAD : RC_RDENSE + partial) + op.k); break;
                     case K_SWAPX: op.code = uint8_t(RC_SWAP + partial + op.k); break;
                     case K_PHASE1: op.code = op.smask == all_slots ? RC_PHASE_ALL : RC_PHASE; break;
                     case K_DIAG: op.code = RC_DIAG; break;
@@ -514,6 +525,9 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
     }
     d.op_count = int(regops.size()) - d.op_begin;
     d.round_count = int(rounds.size()) - d.round_begin;
+    d.pscale_on = pscale != 1.0;
+    d.pscale_hi = float(pscale);
+    d.pscale_lo = float(pscale - double(d.pscale_hi));
     return true;
 }
 
@@ -1385,7 +1399,7 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
         } else {
             add("step %zu TILE b=%d L=%d high=", j, st.d.b, st.d.L);
             for (int h = 0; h < st.d.nh; ++h) add("%d%s", st.d.hpos[h], h + 1 < st.d.nh ? "," : "");
-            add(" ops=%d rounds=%d\n", st.d.op_count, st.d.round_count);
+            add(" ops=%d rounds=%d%s\n", st.d.op_count, st.d.round_count, st.d.pscale_on ? " deferred-scale" : "");
             for (int r = 0; r < st.d.round_count; ++r) {
                 const RoundDesc &rd = p->h_rounds[size_t(st.d.round_begin + r)];
                 const int RB = st.d.b - kRegThreadBits;
@@ -1395,7 +1409,8 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
                 for (int k = 0; k < rd.op_count; ++k) {
                     const RegOp &op = p->h_regops[size_t(st.d.op_begin + rd.op_begin + k)];
                     const int c = op.code;
-                    if (c < RC_PHASE_ALL) add(" %s%s/%d", kinds[c / 8], (c & 4) ? "p" : "", c & 3);
+                    if (c >= RC_HAD) add(" HAD/%d", c - RC_HAD);
+                    else if (c < RC_PHASE_ALL) add(" %s%s/%d", kinds[c / 8], (c & 4) ? "p" : "", c & 3);
                     else if (c == RC_PHASE_ALL || c == RC_PHASE) add(" PHASE");
                     else if (c == RC_DIAG) add(" DIAG");
                     else if (c == RC_SCALE) add(" SCALE");

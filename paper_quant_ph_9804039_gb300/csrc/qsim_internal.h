@@ -89,6 +89,11 @@ struct TilePassDesc {
     int opos[QSIM_MAX_QUBITS];
     int op_begin, op_count;
     int round_begin, round_count;  // register rounds (0 rounds: the shared-memory form)
+    // register rounds: the pass's Hadamards are applied as (a + b, a - b) and
+    // the product of their 1/sqrt(2) factors (a scalar, which commutes with
+    // every op) once at the end, as pscale_hi + pscale_lo, when pscale_on
+    int pscale_on;
+    float pscale_hi, pscale_lo;
 };
 
 template <typename T2>
@@ -171,6 +176,7 @@ enum RegCode : uint8_t {
     RC_SCALE = 27,
     RC_TAB = 28,
     RC_PHRUN = 29,
+    RC_HAD = 32,      // + k: uncontrolled c [[1, 1], [1, -1]], the factor c deferred to the end of the pass
 };
 static_assert(sizeof(RegOp) % 16 == 0, "RegOp is copied in 16-byte units");
 struct RoundDesc {
