@@ -151,68 +151,69 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
         return;
     }
     if ((i0 & op.nmask) != op.nmask) return;  // a control (or the target) outside the slots is 0
+    const uint32_t code = op.code;
     const uint32_t sm = op.smask;
-#define QS_PAIR_CASES(BASE, SWAP, REAL)                                                   \
-    case BASE + 0: pairs<RB, 0, SWAP, REAL, true>(v, op); break;                          \
-    case BASE + 1: pairs<RB, 1, SWAP, REAL, true>(v, op); break;                          \
-    case BASE + 2: pairs<RB, 2, SWAP, REAL, true>(v, op); break;                          \
-    case BASE + 3: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL, true>(v, op); break;    \
-    case BASE + 4: pairs<RB, 0, SWAP, REAL, false>(v, op); break;                         \
-    case BASE + 5: pairs<RB, 1, SWAP, REAL, false>(v, op); break;                         \
-    case BASE + 6: pairs<RB, 2, SWAP, REAL, false>(v, op); break;                         \
-    case BASE + 7: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL, false>(v, op); break;
-    switch (op.code) {
-        QS_PAIR_CASES(RC_DENSE, false, false)
-        QS_PAIR_CASES(RC_RDENSE, false, true)
-        QS_PAIR_CASES(RC_SWAP, true, false)
-        case RC_HAD + 0: pairs_had<RB, 0>(v); break;
-        case RC_HAD + 1: pairs_had<RB, 1>(v); break;
-        case RC_HAD + 2: pairs_had<RB, 2>(v); break;
-        case RC_HAD + 3: if constexpr (RB > 3) pairs_had<RB, 3>(v); break;
-        case RC_PHASE_ALL: {
+    // an if-tree of small switches, the common kinds first (the Hadamard is
+    // taken by the caller): one switch over every code was measured at about
+    // twice the cost per op
+    if (code == RC_TAB) {
+        uint32_t g = 0;  // index bits held by the thread's base index
+        for (int j = 0; j < op.tw; ++j) g |= ((i0 >> op.tpos[j]) & 1u) << j;
+        const float4 *tab = reinterpret_cast<const float4 *>(runs + op.tab_off);
 #pragma unroll
-            for (int c = 0; c < S; ++c) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
-            break;
+        for (int c = 0; c < S; ++c) {
+            if (!((sm >> c) & 1u)) continue;
+            const float4 t = __ldg(tab + (g | op.cidx[c]));
+            v.x[c] = cmulx(make_float2(t.x, t.y), make_float2(t.z, t.w), v.x[c]);
         }
-        case RC_PHASE: {
-#pragma unroll
-            for (int c = 0; c < S; ++c)
-                if ((sm >> c) & 1u) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
-            break;
-        }
-        case RC_DIAG: {
-            const bool up_thread = (i0 & op.tbn) != 0;
-#pragma unroll
-            for (int c = 0; c < S; ++c) {
-                if (!((sm >> c) & 1u)) continue;
-                const bool up = op.tbn ? up_thread : ((op.tsel >> c) & 1u);
-                v.x[c] = up ? cmulx(op.u[3], op.ul[3], v.x[c]) : cmulx(op.u[0], op.ul[0], v.x[c]);
-            }
-            break;
-        }
-        case RC_SCALE: {
-            const bool up = (base & op.gsel) != 0;
-            const float2 f = up ? op.u[3] : op.u[0], fl = up ? op.ul[3] : op.ul[0];
-#pragma unroll
-            for (int c = 0; c < S; ++c)
-                if ((sm >> c) & 1u) v.x[c] = cmulx(f, fl, v.x[c]);
-            break;
-        }
-        case RC_TAB: {
-            uint32_t g = 0;  // index bits held by the thread's base index
-            for (int j = 0; j < op.tw; ++j) g |= ((i0 >> op.tpos[j]) & 1u) << j;
-            const float4 *tab = reinterpret_cast<const float4 *>(runs + op.tab_off);
-#pragma unroll
-            for (int c = 0; c < S; ++c) {
-                if (!((sm >> c) & 1u)) continue;
-                const float4 t = __ldg(tab + (g | op.cidx[c]));
-                v.x[c] = cmulx(make_float2(t.x, t.y), make_float2(t.z, t.w), v.x[c]);
-            }
-            break;
-        }
-        default: break;
+        return;
     }
-#undef QS_PAIR_CASES
+#define QS_PAIR_SWITCH(BASE, SWAP, REAL)                                                     \
+    switch (code - BASE) {                                                                    \
+        case 0: pairs<RB, 0, SWAP, REAL, true>(v, op); break;                                 \
+        case 1: pairs<RB, 1, SWAP, REAL, true>(v, op); break;                                 \
+        case 2: pairs<RB, 2, SWAP, REAL, true>(v, op); break;                                 \
+        case 3: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL, true>(v, op); break;           \
+        case 4: pairs<RB, 0, SWAP, REAL, false>(v, op); break;                                \
+        case 5: pairs<RB, 1, SWAP, REAL, false>(v, op); break;                                \
+        case 6: pairs<RB, 2, SWAP, REAL, false>(v, op); break;                                \
+        default: if constexpr (RB > 3) pairs<RB, 3, SWAP, REAL, false>(v, op); break;         \
+    }
+    if (code < RC_RDENSE) {
+        QS_PAIR_SWITCH(RC_DENSE, false, false)
+        return;
+    }
+    if (code < RC_SWAP) {
+        QS_PAIR_SWITCH(RC_RDENSE, false, true)
+        return;
+    }
+    if (code < RC_PHASE_ALL) {
+        QS_PAIR_SWITCH(RC_SWAP, true, false)
+        return;
+    }
+#undef QS_PAIR_SWITCH
+    if (code == RC_PHASE_ALL) {
+#pragma unroll
+        for (int c = 0; c < S; ++c) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
+    } else if (code == RC_PHASE) {
+#pragma unroll
+        for (int c = 0; c < S; ++c)
+            if ((sm >> c) & 1u) v.x[c] = cmulx(op.u[3], op.ul[3], v.x[c]);
+    } else if (code == RC_DIAG) {
+        const bool up_thread = (i0 & op.tbn) != 0;
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            if (!((sm >> c) & 1u)) continue;
+            const bool up = op.tbn ? up_thread : ((op.tsel >> c) & 1u);
+            v.x[c] = up ? cmulx(op.u[3], op.ul[3], v.x[c]) : cmulx(op.u[0], op.ul[0], v.x[c]);
+        }
+    } else if (code == RC_SCALE) {
+        const bool up = (base & op.gsel) != 0;
+        const float2 f = up ? op.u[3] : op.u[0], fl = up ? op.ul[3] : op.ul[0];
+#pragma unroll
+        for (int c = 0; c < S; ++c)
+            if ((sm >> c) & 1u) v.x[c] = cmulx(f, fl, v.x[c]);
+    }
 }
 
 template <int RB>
@@ -276,6 +277,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_tile_reg(float2 *dst, const flo
             }
             for (int k = R.op_begin; k < R.op_begin + R.op_count; ++k) {
                 const RegOp &op = sops[k];
+                const uint32_t code = op.code;
+                if (code >= RC_HAD) {  // the commonest op, before any other test (no controls by construction)
+                    switch (code - RC_HAD) {
+                        case 0: pairs_had<RB, 0>(v); break;
+                        case 1: pairs_had<RB, 1>(v); break;
+                        case 2: pairs_had<RB, 2>(v); break;
+                        default: if constexpr (RB > 3) pairs_had<RB, 3>(v); break;
+                    }
+                    continue;
+                }
                 if (op.gmask && (base & op.gmask) != op.gmask) continue;  // uniform over the block
                 apply_op<RB>(v, op, i0, R, base, tile, d, runs, ps, nrun);
             }
