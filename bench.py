@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--workload", default="qft-m28-c64", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="tiled", choices=["auto", "tiled", "unfused", "fused"])
     ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--no-specialize", action="store_true",
+                    help="keep the general register kernel instead of one generated kernel per tile pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -213,8 +215,12 @@ def run_ours(args, rank, world, local):
     ideal = qs.State(M, device=dev, stream=stream, zero=False)
     noisy = qs.State(M, device=dev, stream=stream, zero=False)
     mode = args.mode
-    p_ideal = qs.Plan(M, c["ideal"], mode=mode, tile_bits=args.tile_bits)
-    p_noisy = qs.Plan(M, c["noisy"], mode=mode, tile_bits=args.tile_bits)
+    spec = not args.no_specialize
+    t_plan = time.perf_counter()
+    p_ideal = qs.Plan(M, c["ideal"], mode=mode, tile_bits=args.tile_bits, specialize=spec)
+    p_noisy = qs.Plan(M, c["noisy"], mode=mode, tile_bits=args.tile_bits, specialize=spec)
+    t_plan = time.perf_counter() - t_plan
+    specialised = "specialised" in p_noisy.describe()
     st_i, st_n = p_ideal.stats(), p_noisy.stats()
     amp_updates_step = 2.0 * n_logical * float(1 << M)
     launches_step = st_i["n_launches"] + st_n["n_launches"] + 2
@@ -275,7 +281,9 @@ def run_ours(args, rank, world, local):
         "config": {"workload": args.workload, "M": M, "circuit": "qft", "sigma": wl["sigma"],
                    "gates_per_circuit": n_logical, "gate_records_per_circuit": int(len(c["noisy"])),
                    "circuits_per_step": 2, "mode": mode, "tile_bits": st_n["tile_bits"],
-                   "passes_per_circuit": st_n["n_passes"], "l2": f"inputs larger than L2 ({(8 << M) >> 20} MiB per state)",
+                   "passes_per_circuit": st_n["n_passes"], "specialised_passes": specialised,
+                   "plan_create_s": round(t_plan, 3),
+                   "l2": f"inputs larger than L2 ({(8 << M) >> 20} MiB per state)",
                    "parallelism": f"replicas{world}"},
         "roofline": roofline,
         "gpu_launches": int(launches_step * args.steps),

@@ -87,6 +87,10 @@ typedef struct qsim_opts {
                          * mode needs complex64 and M >= 12, and falls back to TILED otherwise */
     int32_t tile_bits;  /* QSIM_MODE_TILED tile size 2^tile_bits amplitudes, 6..13; 0 = default */
     int32_t use_graph;  /* 1: a plan replays its launches as one captured CUDA graph */
+    int32_t specialize; /* 1: each complex64 register tile pass is generated as its own kernel (op kinds,
+                         * masks and matrix entries as constants) and compiled with NVRTC at plan
+                         * creation: slower creation (about a second), faster execution, same
+                         * results; without NVRTC the plan keeps the general kernel */
 } qsim_opts;
 
 /* Counts describing one execution of a plan. */

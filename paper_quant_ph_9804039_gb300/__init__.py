@@ -44,7 +44,7 @@ class QsimError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("fuse_k", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -172,9 +172,9 @@ def _records(gates) -> np.ndarray:
     return np.ascontiguousarray(gates, dtype=GATE_DTYPE)
 
 
-def _opts(mode="auto", fuse_k=0, tile_bits=0, use_graph=False) -> Opts:
+def _opts(mode="auto", fuse_k=0, tile_bits=0, use_graph=False, specialize=False) -> Opts:
     m = _MODES[mode] if isinstance(mode, str) else int(mode)
-    return Opts(m, int(fuse_k), int(tile_bits), int(bool(use_graph)))
+    return Opts(m, int(fuse_k), int(tile_bits), int(bool(use_graph)), int(bool(specialize)))
 
 
 def _torch():
@@ -290,13 +290,14 @@ def fidelity(ideal: State, noisy: State):
 class Plan:
     """A compiled circuit for states of M qubits (qsim_plan_create)."""
 
-    def __init__(self, M: int, gates, prec="c64", mode="auto", fuse_k=0, tile_bits=0, use_graph=False):
+    def __init__(self, M: int, gates, prec="c64", mode="auto", fuse_k=0, tile_bits=0, use_graph=False,
+                 specialize=False):
         lib = load_library()
         self.M = int(M)
         self.prec = _prec(prec)
         g = _records(gates)
         self.n_gates = len(g)
-        o = _opts(mode, fuse_k, tile_bits, use_graph)
+        o = _opts(mode, fuse_k, tile_bits, use_graph, specialize)
         h = _vp()
         _check(lib.qsim_plan_create(self.M, self.prec, _vp(g.ctypes.data), len(g), ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -24,7 +24,10 @@ LIB = os.path.join(LIBDIR, "libqsim.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-              "-I", INCLUDE, "-I", CSRC]
+              "-I", INCLUDE, "-I", CSRC, "-I", BUILD]
+# device helpers of the specialised passes, embedded as a string for NVRTC
+JIT_HEADER = os.path.join(CSRC, "jit_device.cuh")
+JIT_INC = os.path.join(BUILD, "jit_device_src.inc")
 
 
 def nvcc() -> str:
@@ -63,16 +66,26 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+def _embed_jit_header():
+    with open(JIT_HEADER) as f:
+        text = f.read()
+    if ")QSJIT" in text:
+        raise RuntimeError("jit_device.cuh may not contain the raw-string delimiter")
+    with open(JIT_INC, "w") as f:
+        f.write('R"QSJIT(' + text + ')QSJIT"\n')
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
+    _embed_jit_header()
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-Xlinker", "--no-undefined"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-ldl", "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

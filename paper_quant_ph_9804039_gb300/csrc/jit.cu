@@ -1,0 +1,340 @@
+// Specialised register tile passes (qsim_opts.specialize).
+//
+// The general register kernel (k_tile_reg.cu) reads each op's kind, slot bit,
+// masks and matrix from shared memory and dispatches at run time; with a few
+// floating-point operations per amplitude per gate, that dispatch is most of
+// its instruction stream.  Here every register tile pass of a plan becomes its
+// own kernel, generated as CUDA source at plan creation with the pass's tile
+// layout, rounds, op kinds, slot masks and matrix entries as literals, and
+// compiled by NVRTC for sm_103a into one cubin per plan.  The arithmetic is
+// that of the general kernel (Section 2.1's pair update with compensated
+// entries; runs of phase gates as one phase polynomial), op by op in the same
+// order, so results are bitwise those of the general kernel up to the
+// compiler's scheduling of independent operations.  NVRTC is loaded with
+// dlopen on first use; without it, or if compilation fails, the plan keeps the
+// general kernel (qsim_plan_describe says which).
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qsim_internal.h"
+
+namespace qs {
+namespace {
+
+const char *const kJitHeader =
+#include "jit_device_src.inc"
+    ;
+
+// ------------------------------------------------------------------ NVRTC
+struct Nvrtc {
+    bool tried = false, ok = false;
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+};
+
+Nvrtc &nvrtc() {
+    static Nvrtc n;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (n.tried) return n;
+    n.tried = true;
+    const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                           "/usr/local/cuda/lib64/libnvrtc.so"};
+    void *h = nullptr;
+    for (const char *nm : names)
+        if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) return n;
+    n.create = reinterpret_cast<decltype(n.create)>(dlsym(h, "nvrtcCreateProgram"));
+    n.compile = reinterpret_cast<decltype(n.compile)>(dlsym(h, "nvrtcCompileProgram"));
+    n.log_size = reinterpret_cast<decltype(n.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+    n.log = reinterpret_cast<decltype(n.log)>(dlsym(h, "nvrtcGetProgramLog"));
+    n.cubin_size = reinterpret_cast<decltype(n.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+    n.cubin = reinterpret_cast<decltype(n.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+    n.destroy = reinterpret_cast<decltype(n.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+    n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+    return n;
+}
+
+// ------------------------------------------------------------- generation
+struct Src {
+    std::string s;
+    void operator()(const char *fmt, ...) __attribute__((format(printf, 2, 3))) {
+        char buf[1024];
+        va_list ap;
+        va_start(ap, fmt);
+        std::vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        s += buf;
+    }
+};
+
+std::string flit(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    char b[48];
+    std::snprintf(b, sizeof b, "__int_as_float(0x%08x)", u);
+    return b;
+}
+std::string f2lit(float2 v) { return "make_float2(" + flit(v.x) + ", " + flit(v.y) + ")"; }
+
+// Slots of a round: bit k of slot index c <-> tile position pos[k].
+uint32_t dep_of(const RoundDesc &rd, int RB, int c) {
+    uint32_t o = 0;
+    for (int k = 0; k < RB; ++k)
+        if ((c >> k) & 1) o |= 1u << rd.pos[k];
+    return o;
+}
+
+void emit_pairs(Src &out, const RegOp &op, int RB, const char *kind) {
+    const int S = 1 << RB, K = op.k;
+    for (int c = 0; c < S; ++c) {
+        if ((c >> K) & 1) continue;
+        if (!((op.smask >> c) & 1)) continue;
+        const int c1 = c | (1 << K);
+        if (!std::strcmp(kind, "swap")) {
+            out("    { const float2 t = v[%d]; v[%d] = v[%d]; v[%d] = t; }\n", c, c, c1, c1);
+        } else if (!std::strcmp(kind, "had")) {
+            out("    { const float2 a = v[%d], b = v[%d]; v[%d] = make_float2(a.x + b.x, a.y + b.y); "
+                "v[%d] = make_float2(a.x - b.x, a.y - b.y); }\n",
+                c, c1, c, c1);
+        } else if (!std::strcmp(kind, "real")) {
+            out("    { const float2 a = v[%d], b = v[%d]; v[%d] = qs_rmad2x(%s, %s, a, %s, %s, b); "
+                "v[%d] = qs_rmad2x(%s, %s, a, %s, %s, b); }\n",
+                c, c1, c, flit(op.u[0].x).c_str(), flit(op.ul[0].x).c_str(), flit(op.u[1].x).c_str(),
+                flit(op.ul[1].x).c_str(), c1, flit(op.u[2].x).c_str(), flit(op.ul[2].x).c_str(),
+                flit(op.u[3].x).c_str(), flit(op.ul[3].x).c_str());
+        } else {
+            out("    { const float2 a = v[%d], b = v[%d]; v[%d] = qs_cmad2x(U0, L0, a, U1, L1, b); "
+                "v[%d] = qs_cmad2x(U2, L2, a, U3, L3, b); }\n",
+                c, c1, c, c1);
+        }
+    }
+}
+
+void emit_op(Src &out, const RegOp &op, const RoundDesc &rd, int RB, const TilePassDesc &d,
+             const std::vector<unsigned char> &runs) {
+    const int S = 1 << RB;
+    const int code = op.code;
+    if (code == RC_PHRUN) {
+        PhaseRunHdr h;
+        std::memcpy(&h, runs.data() + op.gsel, sizeof h);
+        out("  {  // phase run\n");
+        out("    const unsigned char *rec = runs + %llu;\n", (unsigned long long)op.gsel);
+        out("    const int buf = nrun & 1; ++nrun;\n");
+        out("    qs_phrun_setup<%d, %d>(rec, tile, kTq, kOpos, ps_cl[buf], ps_ktw[buf]);\n", d.b, d.nout);
+        out("    const qs_u32 *Q = reinterpret_cast<const qs_u32 *>(rec + %u);\n", h.q_offset);
+        out("    const qs_u32 q0 = __ldg(Q + i0);\n");
+        out("    qs_u32 phi = __ldg(reinterpret_cast<const qs_u32 *>(rec + sizeof(QsPhaseRunHdr))) + q0;\n");
+        out("    #pragma unroll\n    for (int j = 0; j < 8; ++j) phi += ps_ktw[buf][j];\n");
+        out("    #pragma unroll\n    for (int t = 0; t < %d; ++t) if ((i0 >> t) & 1u) phi += ps_cl[buf][t];\n", d.b);
+        out("    float2 e[%d];\n    e[0] = qs_expi(phi);\n", S);
+        for (int k = 0; k < RB; ++k) {
+            out("    { const float2 dk = qs_expi(ps_cl[buf][%d] + __ldg(Q + (i0 | %uu)) - q0);\n", rd.pos[k],
+                1u << rd.pos[k]);
+            for (int c = 0; c < (1 << k); ++c) out("      e[%d] = qs_cmul(e[%d], dk);\n", c | (1 << k), c);
+            out("    }\n");
+        }
+        out("    const float2 *f = reinterpret_cast<const float2 *>(runs + %u);\n", op.tab_off);
+        for (int c = 0; c < S; ++c) out("    v[%d] = qs_cmul(qs_cmul(e[%d], __ldg(f + %d)), v[%d]);\n", c, c, c, c);
+        out("  }\n");
+        return;
+    }
+    out("  {\n");
+    if (op.gmask) out("   if ((base & %lluull) == %lluull)\n", (unsigned long long)op.gmask, (unsigned long long)op.gmask);
+    if (op.nmask) out("   if ((i0 & %uu) == %uu)\n", op.nmask, op.nmask);
+    out("   {\n");
+    if (code >= RC_HAD) {
+        emit_pairs(out, op, RB, "had");
+    } else if (code < RC_PHASE_ALL) {
+        const int fam = code / 8;  // 0 dense, 1 real, 2 swap
+        if (fam == 0)
+            for (int j = 0; j < 4; ++j)
+                out("    const float2 U%d = %s, L%d = %s;\n", j, f2lit(op.u[j]).c_str(), j, f2lit(op.ul[j]).c_str());
+        emit_pairs(out, op, RB, fam == 0 ? "dense" : (fam == 1 ? "real" : "swap"));
+    } else if (code == RC_PHASE_ALL || code == RC_PHASE) {
+        out("    const float2 U3 = %s, L3 = %s;\n", f2lit(op.u[3]).c_str(), f2lit(op.ul[3]).c_str());
+        for (int c = 0; c < S; ++c)
+            if ((op.smask >> c) & 1) out("    v[%d] = qs_cmulx(U3, L3, v[%d]);\n", c, c);
+    } else if (code == RC_DIAG) {
+        out("    const float2 U0 = %s, L0 = %s, U3 = %s, L3 = %s;\n", f2lit(op.u[0]).c_str(), f2lit(op.ul[0]).c_str(),
+            f2lit(op.u[3]).c_str(), f2lit(op.ul[3]).c_str());
+        if (op.tbn) out("    const bool up = (i0 & %uu) != 0;\n", op.tbn);
+        for (int c = 0; c < S; ++c) {
+            if (!((op.smask >> c) & 1)) continue;
+            if (op.tbn)
+                out("    v[%d] = up ? qs_cmulx(U3, L3, v[%d]) : qs_cmulx(U0, L0, v[%d]);\n", c, c, c);
+            else if ((op.tsel >> c) & 1)
+                out("    v[%d] = qs_cmulx(U3, L3, v[%d]);\n", c, c);
+            else
+                out("    v[%d] = qs_cmulx(U0, L0, v[%d]);\n", c, c);
+        }
+    } else if (code == RC_SCALE) {
+        out("    const bool up = (base & %lluull) != 0;\n", (unsigned long long)op.gsel);
+        out("    const float2 F = up ? %s : %s, FL = up ? %s : %s;\n", f2lit(op.u[3]).c_str(), f2lit(op.u[0]).c_str(),
+            f2lit(op.ul[3]).c_str(), f2lit(op.ul[0]).c_str());
+        for (int c = 0; c < S; ++c)
+            if ((op.smask >> c) & 1) out("    v[%d] = qs_cmulx(F, FL, v[%d]);\n", c, c);
+    } else if (code == RC_TAB) {
+        out("    const float4 *tab = reinterpret_cast<const float4 *>(runs + %u);\n", op.tab_off);
+        out("    const qs_u32 g = 0u");
+        for (int j = 0; j < op.tw; ++j) out(" | (((i0 >> %d) & 1u) << %d)", op.tpos[j], j);
+        out(";\n");
+        for (int c = 0; c < S; ++c) {
+            if (!((op.smask >> c) & 1)) continue;
+            out("    { const float4 t = __ldg(tab + (g | %uu)); v[%d] = qs_cmulx(make_float2(t.x, t.y), "
+                "make_float2(t.z, t.w), v[%d]); }\n",
+                unsigned(op.cidx[c]), c, c);
+        }
+    }
+    out("   }\n  }\n");
+}
+
+std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &regops,
+                      const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs) {
+    const int RB = d.b - kRegThreadBits, S = 1 << RB;
+    Src out;
+    int tq[32];
+    for (int t = 0; t < d.b; ++t) tq[t] = t < d.L ? t : d.hpos[t - d.L];
+    out("__constant__ int kTq_%d[%d] = {", idx, d.b);
+    for (int t = 0; t < d.b; ++t) out("%d%s", tq[t], t + 1 < d.b ? ", " : "};\n");
+    out("__constant__ int kOpos_%d[%d] = {", idx, d.nout > 0 ? d.nout : 1);
+    if (d.nout == 0) out("0};\n");
+    for (int k = 0; k < d.nout; ++k) out("%d%s", d.opos[k], k + 1 < d.nout ? ", " : "};\n");
+    out("extern \"C\" __global__ void __launch_bounds__(256, 3)\n");
+    out("qs_pass_%d(float2 *dst, const float2 *src, const unsigned char *__restrict__ runs, qs_u64 ntiles) {\n", idx);
+    out("  const int *kTq = kTq_%d; const int *kOpos = kOpos_%d; (void)kTq; (void)kOpos;\n", idx, idx);
+    if (d.round_count > 1) out("  __shared__ float2 s[%d];\n", 1 << d.b);
+    out("  __shared__ qs_u32 ps_cl[2][16], ps_ktw[2][8];\n  int nrun = 0; (void)nrun;\n");
+    out("  const qs_u32 tid = threadIdx.x;\n  float2 v[%d];\n", S);
+    out("  for (qs_u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {\n");
+    out("   qs_u64 base = 0");
+    for (int k = 0; k < d.nout; ++k) out(" | (((tile >> %d) & 1ull) << %d)", k, d.opos[k]);
+    out(";\n");
+    const uint32_t lowmask = (1u << d.L) - 1;
+    auto goff_const = [&](uint32_t i) {  // device offset of tile-local index i
+        uint64_t o = i & lowmask;
+        for (int h = 0; h < d.nh; ++h)
+            if ((i >> (d.L + h)) & 1) o |= uint64_t(1) << d.hpos[h];
+        return o;
+    };
+    auto swz = [](uint32_t x) { return x ^ ((x >> 4) & 15u); };
+    for (int r = 0; r < d.round_count; ++r) {
+        const RoundDesc &rd = rounds[size_t(d.round_begin + r)];
+        out("   {  // round %d\n", r);
+        out("   qs_u32 i0 = tid;\n");
+        for (int k = 0; k < RB; ++k) {
+            const int q = rd.pos[k];
+            out("   i0 = ((i0 >> %d) << %d) | (i0 & %uu);\n", q, q + 1, (1u << q) - 1);
+        }
+        if (r == 0 || r + 1 == d.round_count) {
+            out("   const qs_u64 gi0 = (qs_u64)(i0 & %uu)", lowmask);
+            for (int h = 0; h < d.nh; ++h) out(" | ((qs_u64)((i0 >> %d) & 1u) << %d)", d.L + h, d.hpos[h]);
+            out(";\n");
+        }
+        if (d.round_count > 1) out("   const qs_u32 si0 = i0 ^ ((i0 >> 4) & 15u);\n");
+        if (r == 0) {
+            for (int c = 0; c < S; ++c)
+                out("   v[%d] = src[base | gi0 | %lluull];\n", c, (unsigned long long)goff_const(dep_of(rd, RB, c)));
+        } else {
+            for (int c = 0; c < S; ++c) out("   v[%d] = s[si0 ^ %uu];\n", c, swz(dep_of(rd, RB, c)));
+        }
+        for (int k = 0; k < rd.op_count; ++k)
+            emit_op(out, regops[size_t(d.op_begin + rd.op_begin + k)], rd, RB, d, runs);
+        if (r + 1 == d.round_count) {
+            if (d.pscale_on)
+                for (int c = 0; c < S; ++c)
+                    out("   v[%d] = make_float2(fmaf(v[%d].x, %s, v[%d].x * %s), fmaf(v[%d].y, %s, v[%d].y * %s));\n", c,
+                        c, flit(d.pscale_hi).c_str(), c, flit(d.pscale_lo).c_str(), c, flit(d.pscale_hi).c_str(), c,
+                        flit(d.pscale_lo).c_str());
+            for (int c = 0; c < S; ++c)
+                out("   dst[base | gi0 | %lluull] = v[%d];\n", (unsigned long long)goff_const(dep_of(rd, RB, c)), c);
+        } else {
+            out("   __syncthreads();\n");
+            for (int c = 0; c < S; ++c) out("   s[si0 ^ %uu] = v[%d];\n", swz(dep_of(rd, RB, c)), c);
+            out("   __syncthreads();\n");
+        }
+        out("   }\n");
+    }
+    out("  }\n}\n\n");
+    return out.s;
+}
+
+}  // namespace
+
+int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
+              const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs, cudaLibrary_t *lib,
+              std::vector<cudaKernel_t> *kernels, std::string *log) {
+    Nvrtc &n = nvrtc();
+    if (!n.ok) {
+        if (log) *log = "NVRTC not found";
+        return QSIM_EUNSUPPORTED;
+    }
+    std::string src = kJitHeader;
+    for (size_t i = 0; i < passes.size(); ++i) src += emit_pass(int(i), *passes[i], regops, rounds, runs);
+    nvrtcProgram prog;
+    if (n.create(&prog, src.c_str(), "qsim_passes.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        if (log) *log = "nvrtcCreateProgram failed";
+        return QSIM_EUNSUPPORTED;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17"};
+    const nvrtcResult rc = n.compile(prog, 2, opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        n.log_size(prog, &ls);
+        std::string l(ls, '\0');
+        if (ls) n.log(prog, &l[0]);
+        if (log) *log = "NVRTC compilation failed: " + l.substr(0, 2000);
+        n.destroy(&prog);
+        return QSIM_EUNSUPPORTED;
+    }
+    size_t cs = 0;
+    n.cubin_size(prog, &cs);
+    std::vector<char> cubin(cs);
+    n.cubin(prog, cubin.data());
+    n.destroy(&prog);
+    cudaError_t e = cudaLibraryLoadData(lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "loading the specialised passes");
+    kernels->assign(passes.size(), nullptr);
+    for (size_t i = 0; i < passes.size(); ++i) {
+        char name[32];
+        std::snprintf(name, sizeof name, "qs_pass_%zu", i);
+        e = cudaLibraryGetKernel(&(*kernels)[i], *lib, name);
+        if (e != cudaSuccess) {
+            cudaLibraryUnload(*lib);
+            *lib = nullptr;
+            return cuda_fail(e, "finding a specialised pass");
+        }
+    }
+    return QSIM_OK;
+}
+
+void jit_release(cudaLibrary_t lib) {
+    if (lib) cudaLibraryUnload(lib);
+}
+
+int launch_jit_pass(cudaKernel_t k, void *dst, const void *src, int M, const TilePassDesc &d, const void *runs_dev,
+                    cudaStream_t s) {
+    unsigned long long ntiles = 1ull << (M - d.b);
+    uint64_t grid = uint64_t(num_sms()) * 3;  // __launch_bounds__(256, 3), one wave of resident blocks
+    if (grid > ntiles) grid = ntiles;
+    void *dp = dst;
+    const void *sp = src;
+    const void *rp = runs_dev;
+    void *args[] = {&dp, &sp, &rp, &ntiles};
+    QS_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(k), dim3(unsigned(grid)), dim3(256), args, 0, s));
+    return QSIM_OK;
+}
+
+}  // namespace qs

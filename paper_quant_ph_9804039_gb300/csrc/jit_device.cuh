@@ -1,0 +1,73 @@
+// Device helpers of the specialised tile-pass kernels (compiled at plan
+// creation by NVRTC, see jit.cu).  Self-contained: NVRTC sees no host
+// headers.  The same arithmetic as cx.cuh and k_tile_reg.cu: Section 2.1's
+// pair update with compensated (hi + lo) gate entries, and runs of phase gates
+// as a phase polynomial of the index bits in fixed-point turns of 2^-32.
+
+typedef unsigned int qs_u32;
+typedef unsigned long long qs_u64;
+
+__device__ __forceinline__ float2 qs_cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// (uh + ul) * a
+__device__ __forceinline__ float2 qs_cmulx(float2 uh, float2 ul, float2 a) {
+    const float lre = fmaf(ul.x, a.x, -ul.y * a.y);
+    const float lim = fmaf(ul.x, a.y, ul.y * a.x);
+    return make_float2(fmaf(uh.x, a.x, fmaf(-uh.y, a.y, lre)), fmaf(uh.x, a.y, fmaf(uh.y, a.x, lim)));
+}
+// (uh + ul) * a + (vh + vl) * b
+__device__ __forceinline__ float2 qs_cmad2x(float2 uh, float2 ul, float2 a, float2 vh, float2 vl, float2 b) {
+    const float lre = fmaf(ul.x, a.x, fmaf(-ul.y, a.y, fmaf(vl.x, b.x, -vl.y * b.y)));
+    const float lim = fmaf(ul.x, a.y, fmaf(ul.y, a.x, fmaf(vl.x, b.y, vl.y * b.x)));
+    const float re = fmaf(uh.x, a.x, fmaf(-uh.y, a.y, fmaf(vh.x, b.x, fmaf(-vh.y, b.y, lre))));
+    const float im = fmaf(uh.x, a.y, fmaf(uh.y, a.x, fmaf(vh.x, b.y, fmaf(vh.y, b.x, lim))));
+    return make_float2(re, im);
+}
+// real entries (u + ul) a + (w + wl) b per component
+__device__ __forceinline__ float2 qs_rmad2x(float u, float ul, float2 a, float w, float wl, float2 b) {
+    return make_float2(fmaf(u, a.x, fmaf(w, b.x, fmaf(ul, a.x, wl * b.x))),
+                       fmaf(u, a.y, fmaf(w, b.y, fmaf(ul, a.y, wl * b.y))));
+}
+// e^{2 pi i phi / 2^32}: the top 24 bits through sincospif (exact argument),
+// the low 8 bits (< 3.7e-7 rad) as a first-order rotation.
+__device__ __forceinline__ float2 qs_expi(qs_u32 phi) {
+    const int sp = int(phi);
+    const float x = float(sp >> 8) * (1.0f / 8388608.0f);
+    float sn, cs;
+    sincospif(x, &sn, &cs);
+    const float r = float(phi & 255u) * 1.4629180792671596e-09f;
+    return make_float2(fmaf(-sn, r, cs), fmaf(cs, r, sn));
+}
+
+struct QsPhaseRunHdr {
+    qs_u32 M, b, q_offset, pad;
+};
+
+// Per-tile constants of a phase-polynomial record (all threads call it; one
+// barrier): cl[t] = c_{q_t} + sum over set outside bits k of w[q_t][r_k],
+// kt = c0 + sum over set outside bits k <= k2 of (c_{r_k} or w[r_k][r_k2]).
+// tq[t] = device position of tile bit t, opos[k] = of outside bit k.
+template <int B, int NOUT>
+__device__ __forceinline__ void qs_phrun_setup(const unsigned char *__restrict__ rec, qs_u64 tile, const int *tq,
+                                               const int *opos, qs_u32 *cl, qs_u32 *ktw) {
+    const int M = int(reinterpret_cast<const QsPhaseRunHdr *>(rec)->M);
+    const qs_u32 *c = reinterpret_cast<const qs_u32 *>(rec + sizeof(QsPhaseRunHdr)) + 1;
+    const qs_u32 *w = c + M;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool set = lane < NOUT && ((tile >> lane) & 1);
+    const int r = lane < NOUT ? opos[lane] : 0;
+    for (int t = warp; t < B; t += 8) {
+        const qs_u32 v = __reduce_add_sync(0xffffffffu, set ? __ldg(w + tq[t] * M + r) : 0u);
+        if (lane == 0) cl[t] = v + __ldg(c + tq[t]);
+    }
+    qs_u32 kv = 0;
+    for (int p = threadIdx.x; p < NOUT * NOUT; p += 256) {
+        const int k = p / NOUT, k2 = p - k * NOUT;
+        if (k2 < k || !((tile >> k) & 1) || !((tile >> k2) & 1)) continue;
+        kv += k2 == k ? __ldg(c + opos[k]) : __ldg(w + opos[k] * M + opos[k2]);
+    }
+    kv = __reduce_add_sync(0xffffffffu, kv);
+    if (lane == 0) ktw[warp] = kv;
+    __syncthreads();
+}

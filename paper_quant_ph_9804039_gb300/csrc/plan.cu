@@ -56,6 +56,10 @@ struct qsim_plan {
     size_t rounds_bytes = 0;
     std::vector<RegOp> h_regops;  // host copies, for qsim_plan_describe
     std::vector<RoundDesc> h_rounds;
+    // specialised register passes (qsim_opts.specialize): one kernel per step, or null
+    cudaLibrary_t jit_lib = nullptr;
+    std::vector<cudaKernel_t> jit_k;
+    std::string jit_log;
     int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
     int fuse_k = 0;
     // non-null: device tables are allocated and freed stream-ordered on this
@@ -1098,8 +1102,13 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
         if (timed && !first)
             if (int rc = next_event(p, s)) return rc;
         if (st.type == S_TILE && st.d.round_count > 0) {
-            if (int rc = launch_tile_reg(dst, first ? src : dst, p->M, st.d, p->d_regops, p->d_rounds, p->d_runs, s))
+            const size_t si = size_t(&st - p->steps.data());
+            if (si < p->jit_k.size() && p->jit_k[si]) {
+                if (int rc = launch_jit_pass(p->jit_k[si], dst, first ? src : dst, p->M, st.d, p->d_runs, s)) return rc;
+            } else if (int rc = launch_tile_reg(dst, first ? src : dst, p->M, st.d, p->d_regops, p->d_rounds,
+                                                p->d_runs, s)) {
                 return rc;
+            }
         } else if (st.type == S_TILE) {
             if (int rc = launch_tile_pass(dst, first ? src : dst, p->M, p->prec, st.d, p->d_ops, p->d_runs, s))
                 return rc;
@@ -1246,6 +1255,20 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
                 rc = upload(p, &p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
                 if (rc == QSIM_OK) rc = upload(p, &p->d_regops, regops.data(), regops.size() * sizeof(RegOp), &p->regops_bytes);
                 if (rc == QSIM_OK) rc = upload(p, &p->d_rounds, rounds.data(), rounds.size() * sizeof(RoundDesc), &p->rounds_bytes);
+                if (rc == QSIM_OK && o.specialize) {  // one generated kernel per register pass
+                    std::vector<const TilePassDesc *> descs;
+                    std::vector<size_t> at;
+                    for (size_t si = 0; si < p->steps.size(); ++si)
+                        if (p->steps[si].type == S_TILE && p->steps[si].d.round_count > 0) {
+                            descs.push_back(&p->steps[si].d);
+                            at.push_back(si);
+                        }
+                    std::vector<cudaKernel_t> ks;
+                    if (!descs.empty() && jit_build(descs, regops, rounds, runs, &p->jit_lib, &ks, &p->jit_log) == QSIM_OK) {
+                        p->jit_k.assign(p->steps.size(), nullptr);
+                        for (size_t j = 0; j < at.size(); ++j) p->jit_k[at[j]] = ks[j];
+                    }
+                }
                 p->h_regops = std::move(regops);
                 p->h_rounds = std::move(rounds);
             } else {
@@ -1285,6 +1308,8 @@ void plan_release(qsim_plan *p) {
     dev_free(p, p->d_ops);
     dev_free(p, p->d_runs);
     dev_free(p, p->d_rimg);
+    jit_release(p->jit_lib);
+    p->jit_lib = nullptr;
     dev_free(p, p->d_regops);
     dev_free(p, p->d_rounds);
     dev_free(p, p->d_status);
@@ -1386,6 +1411,7 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
     };
     static const char *kinds[] = {"DENSE", "RDENSE", "SWAP"};
     add("M=%d prec=%s mode=%d steps=%zu\n", p->M, p->prec == QSIM_C64 ? "c64" : "c128", p->mode, p->steps.size());
+    if (!p->jit_log.empty()) add("specialisation: %s\n", p->jit_log.c_str());
     for (size_t j = 0; j < p->steps.size(); ++j) {
         const Step &st = p->steps[j];
         if (st.type == S_GATE) {
@@ -1399,7 +1425,9 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
         } else {
             add("step %zu TILE b=%d L=%d high=", j, st.d.b, st.d.L);
             for (int h = 0; h < st.d.nh; ++h) add("%d%s", st.d.hpos[h], h + 1 < st.d.nh ? "," : "");
-            add(" ops=%d rounds=%d%s\n", st.d.op_count, st.d.round_count, st.d.pscale_on ? " deferred-scale" : "");
+            const bool spec = j < p->jit_k.size() && p->jit_k[j];
+            add(" ops=%d rounds=%d%s%s\n", st.d.op_count, st.d.round_count, st.d.pscale_on ? " deferred-scale" : "",
+                spec ? " specialised" : "");
             for (int r = 0; r < st.d.round_count; ++r) {
                 const RoundDesc &rd = p->h_rounds[size_t(st.d.round_begin + r)];
                 const int RB = st.d.b - kRegThreadBits;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -187,6 +188,14 @@ struct RoundDesc {
 int launch_tile_reg(void *dst, const void *src, int M, const TilePassDesc &d, const void *ops_dev,
                     const void *rounds_dev, const void *runs_dev, cudaStream_t s);
 int tile_reg_prepare();
+// Specialised register passes (jit.cu): generate, compile (NVRTC) and load one
+// kernel per pass; QSIM_EUNSUPPORTED (with *log) when NVRTC is unavailable.
+int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
+              const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs, cudaLibrary_t *lib,
+              std::vector<cudaKernel_t> *kernels, std::string *log);
+void jit_release(cudaLibrary_t lib);
+int launch_jit_pass(cudaKernel_t k, void *dst, const void *src, int M, const TilePassDesc &d, const void *runs_dev,
+                    cudaStream_t s);
 constexpr int kTileOpSmemBytes = 24 * 1024;  // a pass's ops are staged in shared memory up to this size
 int tile_max_bits(qsim_prec prec);
 int tile_prepare(qsim_prec prec);  // one-time kernel attributes (call before any stream capture)

@@ -99,7 +99,7 @@ int start_request(qsim_server *srv, Slot *s) {
     const size_t vec = (size_t(1) << r.M) * 8;
     for (int k = 0; k < 2; ++k)
         QS_CUDA(cudaMallocFromPoolAsync(&s->amps[k], vec, srv->pool, s->stream));
-    qsim_opts po{srv->opts.mode, 0, 0, 0};
+    qsim_opts po{srv->opts.mode, 0, 0, 0, 0};
     if (int rc = plan_create_on(r.M, QSIM_C64, r.ideal.data(), r.ideal.size(), &po, s->stream, &s->plans[0]))
         return rc;
     if (int rc = plan_create_on(r.M, QSIM_C64, r.noisy.data(), r.noisy.size(), &po, s->stream, &s->plans[1]))

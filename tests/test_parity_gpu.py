@@ -435,3 +435,41 @@ def test_fused_out_of_place(orc):
     _close(dst.get(), orc.run(M, recs, x128, nthreads=NT), "c64")
     assert np.array_equal(src.get(), x)
 
+
+
+# -------------------------------------------------- specialised tile passes
+def _spec_circuit(kind, M, rng):
+    if kind == "random":
+        return _rand_gates(rng, M, 150)
+    if kind == "qft":
+        return W.circuit_c2_qft(M, sigma=1e-4)["noisy"]
+    if kind == "brickwork":
+        return W.circuit_c4_brickwork_toffoli(M, layers=6)["noisy"]
+    recs = []  # phase runs between Hadamards, controls inside and outside the tile
+    for _ in range(4):
+        for q in rng.choice(M, size=3, replace=False):
+            recs.append(W.gate_record(W.mat_h(), int(q)))
+        for _ in range(25):
+            t = int(rng.integers(M))
+            c = int(rng.choice([q for q in range(M) if q != t]))
+            recs.append(W.gate_record(W.mat_phase(float(rng.uniform(-7, 7))), t, (c,)))
+    return W._pack(recs)
+
+
+@pytest.mark.parametrize("kind", ["random", "qft", "brickwork", "phase"])
+@pytest.mark.parametrize("M,tile_bits", [(12, 12), (16, 12), (20, 11), (20, 12)])
+def test_specialised_passes(orc, kind, M, tile_bits):
+    """Register tile passes generated as their own kernels (NVRTC) give the
+    general kernel's results bit for bit, and the oracle's within tolerance."""
+    rng = np.random.default_rng(500 + M + tile_bits)
+    recs = _spec_circuit(kind, M, rng)
+    x, x128 = _input(M, "c64")
+    gen = qs.Plan(M, recs, mode="tiled", tile_bits=tile_bits)
+    spec = qs.Plan(M, recs, mode="tiled", tile_bits=tile_bits, specialize=True)
+    assert "specialised" in spec.describe(), spec.describe()[:400]
+    a = qs.State(M).set(x)
+    gen.execute(a)
+    b = qs.State(M).set(x)
+    spec.execute(b)
+    assert np.array_equal(a.get(), b.get())
+    _close(b.get(), orc.run(M, recs, x128, nthreads=NT), "c64")
