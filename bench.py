@@ -263,7 +263,7 @@ def run_ours(args, rank, world, local):
             d[1] += t_bytes[j] * execs
             d[2] += execs
     kname = {0: "k_gate (one gate per launch)", 1: "k_tile_pass", 2: "k_fused_tc", 3: "k_permute",
-             4: "k_tile_reg"}
+             4: "k_tile_reg", 5: "qs_pass (specialised register tile pass)"}
     top = max(kinds, key=lambda k: kinds[k][0])
     tot_ms, tot_bytes, n_launch = kinds[top]
     peak, peak_src = measured_peaks()
@@ -571,8 +571,9 @@ def run_brickwork(args, rank, world, local):
                               ("unfused", 1, 0)):
         if mode == "unfused" and args.no_unfused:
             continue
-        p_i = qs.Plan(M, c["ideal"], mode=mode)
-        p_n = qs.Plan(M, c["noisy"], mode=mode)
+        spec = mode == "tiled" and not args.no_specialize
+        p_i = qs.Plan(M, c["ideal"], mode=mode, specialize=spec)
+        p_n = qs.Plan(M, c["noisy"], mode=mode, specialize=spec)
 
         def step():
             ideal.reset()
@@ -604,6 +605,7 @@ def run_brickwork(args, rank, world, local):
         st = p_n.stats()
         gbs = tot_bytes / (tot_ms / 1e3) / 1e9
         modes[mode] = {"amp_updates_per_s": job_throughput(2.0 * n * float(1 << M), world, ms), "ms_per_step": ms,
+                       "specialised_passes": "specialised" in p_n.describe(),
                        "steps": steps, "warmup": warm, "passes_per_circuit": st["n_passes"],
                        "launch_GB/s": round(gbs, 1), "launch_frac_of_measured_hbm": round(gbs / peak, 4),
                        "F": F, "norm": nrm, "clocks": clk.summary()}

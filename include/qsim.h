@@ -201,7 +201,8 @@ int qsim_plan_set_timing(qsim_plan *plan, int enable);
  * of one execution: ms[j] = milliseconds summed over the timed executions,
  * bytes[j] = algorithmic bytes of that launch, kind[j] = 0 single gate,
  * 1 shared-memory tile pass, 2 fused block, 3 qubit permutation pass,
- * 4 register tile pass (complex64).  *executions = number of timed executions.
+ * 4 register tile pass (complex64), 5 specialised register tile pass.
+ * *executions = number of timed executions.
  * Any output array may be NULL.  Clears the record. */
 int qsim_plan_timing(qsim_plan *plan, int64_t n_max, double *ms, double *bytes, int32_t *kind,
                      int64_t *executions);

@@ -20,13 +20,27 @@ namespace qs {
 namespace {
 
 constexpr int kPermThreads = 256;
-constexpr int kBatch = 8;  // global loads per thread in flight
+
+// One amplitude global -> shared, asynchronously (cp.async; 8 or 16 bytes).
+__device__ __forceinline__ void cp_async_amp(float2 *dst, const float2 *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_amp(double2 *dst, const double2 *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 
 // The first lb tile qubits are qubits 0..lb-1, so a local index u sits at
 // offset (u & (2^lb - 1)) | hoff[u >> lb] of the vector; sig(u) (the local
 // index whose amplitude lands on u) splits the same way over the two parts.
 template <typename T2>
 __global__ void __launch_bounds__(kPermThreads) k_permute(T2 *dst, const T2 *src, PermDesc d, uint64_t ntiles) {
+
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ns = d.ns, lb = d.lb;
     const uint32_t n = 1u << ns, lmask = (1u << lb) - 1, nh = n >> lb;
@@ -66,29 +80,15 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(T2 *dst, const T2 *src
                 base2 |= uint64_t(1) << d.opos[d.opi[j]];
             }
         if (o2 < o) continue;  // the partner's block does this pair
-        // loads in batches of kBatch per thread, all in flight before the
-        // shared-memory stores that consume them
+        // asynchronous copies straight into shared memory: every load of the
+        // block in flight at once, no registers held
         if (o2 != o) {
-            for (uint32_t u0 = threadIdx.x; u0 < n; u0 += kBatch * kPermThreads) {
-                T2 x[kBatch], y[kBatch];
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const uint32_t u = u0 + uint32_t(j) * kPermThreads;
-                    if (u < n) {
-                        const uint64_t off = (u & lmask) | hoff[u >> lb];
-                        x[j] = src[base | off];
-                        y[j] = src[base2 | off];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const uint32_t u = u0 + uint32_t(j) * kPermThreads;
-                    if (u < n) {
-                        A[pad(u)] = x[j];
-                        B[pad(u)] = y[j];
-                    }
-                }
+            for (uint32_t u = threadIdx.x; u < n; u += kPermThreads) {
+                const uint64_t off = (u & lmask) | hoff[u >> lb];
+                cp_async_amp(A + pad(u), src + (base | off));
+                cp_async_amp(B + pad(u), src + (base2 | off));
             }
+            cp_async_wait();
             __syncthreads();
             // tile o lands on tile o2: out[base2 | off(v)] = A[sig^-1(v)] = A[sig(v)]
             for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
@@ -98,19 +98,9 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(T2 *dst, const T2 *src
                 dst[base | off] = B[ps];
             }
         } else {
-            for (uint32_t u0 = threadIdx.x; u0 < n; u0 += kBatch * kPermThreads) {
-                T2 x[kBatch];
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const uint32_t u = u0 + uint32_t(j) * kPermThreads;
-                    if (u < n) x[j] = src[base | (u & lmask) | hoff[u >> lb]];
-                }
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const uint32_t u = u0 + uint32_t(j) * kPermThreads;
-                    if (u < n) A[pad(u)] = x[j];
-                }
-            }
+            for (uint32_t u = threadIdx.x; u < n; u += kPermThreads)
+                cp_async_amp(A + pad(u), src + (base | (u & lmask) | hoff[u >> lb]));
+            cp_async_wait();
             __syncthreads();
             for (uint32_t v = threadIdx.x; v < n; v += blockDim.x)
                 dst[base | (v & lmask) | hoff[v >> lb]] = A[pad(slo[v & lmask] | shi[v >> lb])];

@@ -527,6 +527,25 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
         rounds.push_back(rd);
         rem.swap(keep);
     }
+    // The first round reads device memory and the last writes it, each thread
+    // at its base index with the slot bits filled in: when a slot sits on tile
+    // position 0, 1 or 2 the lanes of a warp are no longer 8 consecutive
+    // amplitudes apart and every access is a partial sector.  Such a round
+    // gets an op-free neighbour whose slots are the top tile positions, which
+    // moves the tile through shared memory instead.
+    auto low_slot = [&](const RoundDesc &r) {
+        for (int k = 0; k < RB; ++k)
+            if (r.pos[k] < 3) return true;
+        return false;
+    };
+    if (d.b >= RB + 3) {
+        RoundDesc io{};
+        for (int k = 0; k < RB; ++k) io.pos[k] = uint8_t(d.b - RB + k);
+        io.op_begin = 0;
+        io.op_count = 0;
+        if (low_slot(rounds[size_t(d.round_begin)])) rounds.insert(rounds.begin() + d.round_begin, io);
+        if (low_slot(rounds.back())) rounds.push_back(io);
+    }
     d.op_count = int(regops.size()) - d.op_begin;
     d.round_count = int(rounds.size()) - d.round_begin;
     d.pscale_on = pscale != 1.0;
@@ -1380,7 +1399,8 @@ int qsim_plan_timing(qsim_plan *p, int64_t n_max, double *ms, double *bytes, int
         if (bytes) bytes[j] = p->steps[j].bytes;
         if (kind) {
             const Step &st = p->steps[j];
-            kind[j] = st.type == S_TILE && st.d.round_count > 0 ? 4 : int32_t(st.type);
+            const bool spec = size_t(j) < p->jit_k.size() && p->jit_k[size_t(j)];
+            kind[j] = st.type == S_TILE && st.d.round_count > 0 ? (spec ? 5 : 4) : int32_t(st.type);
         }
     }
     if (p->ev_used > 0) {
