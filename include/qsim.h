@@ -249,15 +249,21 @@ int qsim_fidelity_noalloc(const void *ideal_amps, const void *noisy_amps, int M,
 typedef struct qsim_traj_opts {
     int32_t fuse_k;     /* reserved for fused blocks: 0 or 1 (one gate at a time) */
     int32_t use_graph;  /* 1: each run replays a captured CUDA graph */
-    int32_t reserved[2];
+    int32_t kernel;     /* 0: autotuned; 1: shared-memory tile kernel; 2: register-round kernel
+                         * generated for the circuit (NVRTC; falls back to 1 without it) */
+    int32_t reserved;
 } qsim_traj_opts;
 
 typedef struct qsim_traj_plan qsim_traj_plan;  /* opaque; owned by the library */
 
 /* Compile a circuit for up to max_T error trajectories (complex64, M in
  * [1, 20]): computes the error-free state, allocates the per-CTA workspaces
- * and picks the tile size by timing the candidates on a short batch (cached
- * per circuit in the process).  The plan owns its own CUDA stream. */
+ * and picks the kernel configuration by timing the candidates on a short
+ * batch (cached per circuit in the process): the shared-memory tile kernel
+ * with tiles of 2^10..2^13 amplitudes, and the register-round kernel
+ * generated for the circuit with 3 or 4 register qubits per thread (the
+ * fusion width of a round) and 1 or 2 resident trajectories per SM.  The plan
+ * owns its own CUDA stream. */
 int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis, size_t n, int max_T,
                           const qsim_traj_opts *opts, qsim_traj_plan **out);
 
@@ -269,6 +275,12 @@ int qsim_traj_plan_run(qsim_traj_plan *plan, const double *eps, int T, double *F
 
 /* Tile size chosen, tile passes per trajectory and the persistent grid size. */
 int qsim_traj_plan_info(const qsim_traj_plan *plan, int *tile_bits, int *n_passes, int *grid);
+
+/* A text description of the chosen kernel and the autotuner's timings of the
+ * candidates (outside the paper; for tuning).  Writes at most len - 1
+ * characters and a NUL into buf (NULL when len is 0); *needed (may be NULL)
+ * = the full length + 1. */
+int qsim_traj_plan_describe(const qsim_traj_plan *plan, char *buf, int64_t len, int64_t *needed);
 
 void qsim_traj_plan_destroy(qsim_traj_plan *plan);
 

@@ -57,7 +57,8 @@ class PlanStats(ctypes.Structure):
 
 
 class TrajOpts(ctypes.Structure):
-    _fields_ = [("fuse_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+    _fields_ = [("fuse_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -120,6 +121,7 @@ SIGNATURES = [
                                              ctypes.POINTER(TrajOpts), ctypes.POINTER(_vp)]),
     ("qsim_traj_plan_run", ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp, _dp]),
     ("qsim_traj_plan_info", ctypes.c_int, [_vp, _ip, _ip, _ip]),
+    ("qsim_traj_plan_describe", ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     ("qsim_traj_plan_destroy", None, [_vp]),
     ("qsim_server_create", ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)]),
     ("qsim_server_submit", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t,
@@ -347,13 +349,13 @@ class Plan:
 class TrajPlan:
     """A circuit compiled for batches of error trajectories (qsim_traj_plan_create)."""
 
-    def __init__(self, M: int, gates, err_axis, max_T: int, use_graph: bool = True):
+    def __init__(self, M: int, gates, err_axis, max_T: int, use_graph: bool = True, kernel: str = "auto"):
         lib = load_library()
         g = _records(gates)
         ax = np.ascontiguousarray(err_axis, dtype=np.float64)
         assert ax.shape == (len(g), 3)
         self.M, self.n, self.max_T = int(M), len(g), int(max_T)
-        o = TrajOpts(0, int(bool(use_graph)))
+        o = TrajOpts(0, int(bool(use_graph)), {"auto": 0, "smem": 1, "register": 2}[kernel], 0)
         h = _vp()
         _check(lib.qsim_traj_plan_create(self.M, _vp(g.ctypes.data), ax.ctypes.data_as(_dp), len(g), self.max_T,
                                          ctypes.byref(o), ctypes.byref(h)))
@@ -373,6 +375,14 @@ class TrajPlan:
         tb, npass, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(_lib.qsim_traj_plan_info(self._h, ctypes.byref(tb), ctypes.byref(npass), ctypes.byref(grid)))
         return {"tile_bits": tb.value, "n_passes": npass.value, "grid": grid.value}
+
+    def describe(self) -> str:
+        """The chosen kernel and the autotuner's candidate timings."""
+        n = ctypes.c_int64(0)
+        _check(_lib.qsim_traj_plan_describe(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(int(n.value))
+        _check(_lib.qsim_traj_plan_describe(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.value.decode()
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -432,7 +442,7 @@ def run_trajectories(M: int, gates, err_axis, eps, fuse_k: int = 0, use_graph: b
     F = np.zeros(T)
     mean = ctypes.c_double()
     var = ctypes.c_double()
-    o = TrajOpts(int(fuse_k), int(bool(use_graph)))
+    o = TrajOpts(int(fuse_k), int(bool(use_graph)), 0, 0)
     _check(lib.qsim_run_trajectories(int(M), _vp(g.ctypes.data), ax.ctypes.data_as(_dp), len(g),
                                      e.ctypes.data_as(_dp), T, ctypes.byref(o), F.ctypes.data_as(_dp),
                                      ctypes.byref(mean), ctypes.byref(var)))

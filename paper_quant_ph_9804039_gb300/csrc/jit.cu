@@ -123,8 +123,17 @@ void emit_pairs(Src &out, const RegOp &op, int RB, const char *kind) {
     }
 }
 
+// Matrix entry k of an op: a literal, or (J >= 0) entry k of the J-th matrix
+// held in shared memory (mu: hi parts, ml: lo parts).
+std::string ment(const RegOp &op, int J, int k, bool lo) {
+    if (J < 0) return f2lit(lo ? op.ul[k] : op.u[k]);
+    char b[48];
+    std::snprintf(b, sizeof b, "%s[%d][%d]", lo ? "ml" : "mu", J, k);
+    return b;
+}
+
 void emit_op(Src &out, const RegOp &op, const RoundDesc &rd, int RB, const TilePassDesc &d,
-             const std::vector<unsigned char> &runs) {
+             const std::vector<unsigned char> &runs, int J = -1) {
     const int S = 1 << RB;
     const int code = op.code;
     if (code == RC_PHRUN) {
@@ -161,15 +170,15 @@ void emit_op(Src &out, const RegOp &op, const RoundDesc &rd, int RB, const TileP
         const int fam = code / 8;  // 0 dense, 1 real, 2 swap
         if (fam == 0)
             for (int j = 0; j < 4; ++j)
-                out("    const float2 U%d = %s, L%d = %s;\n", j, f2lit(op.u[j]).c_str(), j, f2lit(op.ul[j]).c_str());
+                out("    const float2 U%d = %s, L%d = %s;\n", j, ment(op, J, j, false).c_str(), j, ment(op, J, j, true).c_str());
         emit_pairs(out, op, RB, fam == 0 ? "dense" : (fam == 1 ? "real" : "swap"));
     } else if (code == RC_PHASE_ALL || code == RC_PHASE) {
-        out("    const float2 U3 = %s, L3 = %s;\n", f2lit(op.u[3]).c_str(), f2lit(op.ul[3]).c_str());
+        out("    const float2 U3 = %s, L3 = %s;\n", ment(op, J, 3, false).c_str(), ment(op, J, 3, true).c_str());
         for (int c = 0; c < S; ++c)
             if ((op.smask >> c) & 1) out("    v[%d] = qs_cmulx(U3, L3, v[%d]);\n", c, c);
     } else if (code == RC_DIAG) {
-        out("    const float2 U0 = %s, L0 = %s, U3 = %s, L3 = %s;\n", f2lit(op.u[0]).c_str(), f2lit(op.ul[0]).c_str(),
-            f2lit(op.u[3]).c_str(), f2lit(op.ul[3]).c_str());
+        out("    const float2 U0 = %s, L0 = %s, U3 = %s, L3 = %s;\n", ment(op, J, 0, false).c_str(),
+            ment(op, J, 0, true).c_str(), ment(op, J, 3, false).c_str(), ment(op, J, 3, true).c_str());
         if (op.tbn) out("    const bool up = (i0 & %uu) != 0;\n", op.tbn);
         for (int c = 0; c < S; ++c) {
             if (!((op.smask >> c) & 1)) continue;
@@ -182,8 +191,8 @@ void emit_op(Src &out, const RegOp &op, const RoundDesc &rd, int RB, const TileP
         }
     } else if (code == RC_SCALE) {
         out("    const bool up = (base & %lluull) != 0;\n", (unsigned long long)op.gsel);
-        out("    const float2 F = up ? %s : %s, FL = up ? %s : %s;\n", f2lit(op.u[3]).c_str(), f2lit(op.u[0]).c_str(),
-            f2lit(op.ul[3]).c_str(), f2lit(op.ul[0]).c_str());
+        out("    const float2 F = up ? %s : %s, FL = up ? %s : %s;\n", ment(op, J, 3, false).c_str(),
+            ment(op, J, 0, false).c_str(), ment(op, J, 3, true).c_str(), ment(op, J, 0, true).c_str());
         for (int c = 0; c < S; ++c)
             if ((op.smask >> c) & 1) out("    v[%d] = qs_cmulx(F, FL, v[%d]);\n", c, c);
     } else if (code == RC_TAB) {
@@ -271,6 +280,116 @@ std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &
     return out.s;
 }
 
+// The persistent trajectory kernel (see trajectories.cu): each CTA takes
+// the next trajectory from a counter and runs the circuit's passes on its
+// private workspace (2^M amplitudes) in register rounds; at the start of a
+// pass it builds that pass's erroneous matrices (FP64) into shared memory.
+// The first pass starts from |0...0>, the last accumulates the overlap with
+// the error-free state.  Op j of a pass is regops[pass op_begin + j]; its
+// gate is the trajectory op src[j] (index into the plan's op table).
+std::string emit_traj(int M, const std::vector<TilePassDesc> &passes, const std::vector<RegOp> &regops,
+                      const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks) {
+    Src out;
+    int maxops = 1, maxb = 1;
+    bool smem_tile = false;
+    for (const TilePassDesc &d : passes) {
+        maxops = std::max(maxops, d.op_count);
+        maxb = std::max(maxb, d.b);
+        smem_tile |= d.round_count > 1;
+    }
+    for (size_t p = 0; p < passes.size(); ++p) {
+        out("__constant__ int kSrc_%zu[%d] = {", p, std::max<int>(1, int(src[p].size())));
+        if (src[p].empty()) out("0");
+        for (size_t j = 0; j < src[p].size(); ++j) out("%d%s", src[p][j], j + 1 < src[p].size() ? ", " : "");
+        out("};\n");
+    }
+    out("extern \"C\" __global__ void __launch_bounds__(256, %d)\n", min_blocks);
+    out("qs_traj(const QsTrajOp *__restrict__ ops, const double *__restrict__ eps, int n, int T,\n"
+        "        const float2 *__restrict__ ideal, float2 *work, double *__restrict__ F_out, unsigned *counter) {\n");
+    if (smem_tile) out("  __shared__ float2 s[%d];\n", 1 << maxb);
+    out("  __shared__ float2 mu[%d][4], ml[%d][4];\n  __shared__ double red[2][8];\n  __shared__ int s_t;\n", maxops,
+        maxops);
+    out("  float2 *ws = work + ((qs_u64)blockIdx.x << %d);\n", M);
+    out("  const qs_u32 tid = threadIdx.x;\n  float2 v[16];\n");
+    out("  for (;;) {\n   if (tid == 0) s_t = int(atomicAdd(counter, 1u));\n   __syncthreads();\n");
+    out("   const int t = s_t;\n   if (t >= T) break;\n   double ore = 0.0, oim = 0.0;\n");
+    for (size_t p = 0; p < passes.size(); ++p) {
+        const TilePassDesc &d = passes[p];
+        const int RB = d.b - kRegThreadBits, S = 1 << RB;
+        const bool first = p == 0, last = p + 1 == passes.size();
+        out("   {  // pass %zu\n", p);
+        out("   __syncthreads();\n");
+        out("   for (int j = tid; j < %d; j += 256) { const QsTrajOp &op = ops[kSrc_%zu[j]]; "
+            "qs_noisy_matrix(op, eps[(qs_u64)t * n + op.gate], mu[j], ml[j]); }\n",
+            d.op_count, p);
+        out("   __syncthreads();\n");
+        const uint32_t lowmask = (1u << d.L) - 1;
+        auto goff_const = [&](uint32_t i) {
+            uint64_t o = i & lowmask;
+            for (int h = 0; h < d.nh; ++h)
+                if ((i >> (d.L + h)) & 1) o |= uint64_t(1) << d.hpos[h];
+            return o;
+        };
+        auto swz = [](uint32_t x) { return x ^ ((x >> 4) & 15u); };
+        out("   for (qs_u64 tile = 0; tile < %lluull; ++tile) {\n", 1ull << d.nout);
+        out("    const qs_u64 base = 0");
+        for (int k = 0; k < d.nout; ++k) out(" | (((tile >> %d) & 1ull) << %d)", k, d.opos[k]);
+        out(";\n");
+        for (int r = 0; r < d.round_count; ++r) {
+            const RoundDesc &rd = rounds[size_t(d.round_begin + r)];
+            out("    {  // round %d\n    qs_u32 i0 = tid;\n", r);
+            for (int k = 0; k < RB; ++k) {
+                const int q = rd.pos[k];
+                out("    i0 = ((i0 >> %d) << %d) | (i0 & %uu);\n", q, q + 1, (1u << q) - 1);
+            }
+            if (r == 0 || r + 1 == d.round_count) {
+                out("    const qs_u64 gi0 = (qs_u64)(i0 & %uu)", lowmask);
+                for (int h = 0; h < d.nh; ++h) out(" | ((qs_u64)((i0 >> %d) & 1u) << %d)", d.L + h, d.hpos[h]);
+                out(";\n");
+            }
+            if (d.round_count > 1) out("    const qs_u32 si0 = i0 ^ ((i0 >> 4) & 15u);\n");
+            for (int c = 0; c < S; ++c) {
+                const unsigned long long gd = (unsigned long long)goff_const(dep_of(rd, RB, c));
+                if (r == 0 && first)
+                    out("    v[%d] = make_float2((base | gi0 | %lluull) == 0ull ? 1.f : 0.f, 0.f);\n", c, gd);
+                else if (r == 0)
+                    out("    v[%d] = ws[base | gi0 | %lluull];\n", c, gd);
+                else
+                    out("    v[%d] = s[si0 ^ %uu];\n", c, swz(dep_of(rd, RB, c)));
+            }
+            for (int k = 0; k < rd.op_count; ++k) {
+                const int j = rd.op_begin + k;  // op index within the pass
+                std::vector<unsigned char> none;
+                emit_op(out, regops[size_t(d.op_begin + j)], rd, RB, d, none, j);
+            }
+            if (r + 1 == d.round_count) {
+                for (int c = 0; c < S; ++c) {
+                    const unsigned long long gd = (unsigned long long)goff_const(dep_of(rd, RB, c));
+                    if (last)
+                        out("    { const float2 a = ideal[base | gi0 | %lluull]; ore += (double)fmaf(a.x, v[%d].x, a.y * v[%d].y); "
+                            "oim += (double)fmaf(a.x, v[%d].y, -a.y * v[%d].x); }\n",
+                            gd, c, c, c, c);
+                    else
+                        out("    ws[base | gi0 | %lluull] = v[%d];\n", gd, c);
+                }
+            } else {
+                out("    __syncthreads();\n");
+                for (int c = 0; c < S; ++c) out("    s[si0 ^ %uu] = v[%d];\n", swz(dep_of(rd, RB, c)), c);
+                out("    __syncthreads();\n");
+            }
+            out("    }\n");
+        }
+        out("   }\n   }\n");
+    }
+    out("   for (int o = 16; o > 0; o >>= 1) { ore += __shfl_xor_sync(0xffffffffu, ore, o); "
+        "oim += __shfl_xor_sync(0xffffffffu, oim, o); }\n");
+    out("   if ((tid & 31) == 0) { red[0][tid >> 5] = ore; red[1][tid >> 5] = oim; }\n   __syncthreads();\n");
+    out("   if (tid == 0) { double a = 0, b = 0; for (int w = 0; w < 8; ++w) { a += red[0][w]; b += red[1][w]; } "
+        "F_out[t] = a * a + b * b; }\n");
+    out("   __syncthreads();\n  }\n}\n");
+    return out.s;
+}
+
 }  // namespace
 
 int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
@@ -316,6 +435,46 @@ int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector
             *lib = nullptr;
             return cuda_fail(e, "finding a specialised pass");
         }
+    }
+    return QSIM_OK;
+}
+
+int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::vector<RegOp> &regops,
+                   const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks,
+                   cudaLibrary_t *lib, cudaKernel_t *kernel, std::string *log) {
+    Nvrtc &n = nvrtc();
+    if (!n.ok) {
+        if (log) *log = "NVRTC not found";
+        return QSIM_EUNSUPPORTED;
+    }
+    const std::string src_text = std::string(kJitHeader) + emit_traj(M, passes, regops, rounds, src, min_blocks);
+    nvrtcProgram prog;
+    if (n.create(&prog, src_text.c_str(), "qsim_traj.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        if (log) *log = "nvrtcCreateProgram failed";
+        return QSIM_EUNSUPPORTED;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17"};
+    if (n.compile(prog, 2, opts) != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        n.log_size(prog, &ls);
+        std::string l(ls, '\0');
+        if (ls) n.log(prog, &l[0]);
+        if (log) *log = "NVRTC compilation failed: " + l.substr(0, 2000);
+        n.destroy(&prog);
+        return QSIM_EUNSUPPORTED;
+    }
+    size_t cs = 0;
+    n.cubin_size(prog, &cs);
+    std::vector<char> cubin(cs);
+    n.cubin(prog, cubin.data());
+    n.destroy(&prog);
+    cudaError_t e = cudaLibraryLoadData(lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "loading the trajectory kernel");
+    e = cudaLibraryGetKernel(kernel, *lib, "qs_traj");
+    if (e != cudaSuccess) {
+        cudaLibraryUnload(*lib);
+        *lib = nullptr;
+        return cuda_fail(e, "finding the trajectory kernel");
     }
     return QSIM_OK;
 }

@@ -71,3 +71,45 @@ __device__ __forceinline__ void qs_phrun_setup(const unsigned char *__restrict__
     if (lane == 0) ktw[warp] = kv;
     __syncthreads();
 }
+
+// A gate of an error trajectory (Sections 1.4, 2.0): its error-free matrix,
+// the axis n of its error (zero: no error) and its column in the error table.
+// Same layout as TrajOp of trajectories.cu.
+struct QsTrajOp {
+    double U[8];
+    double ax[3];
+    int gate;
+    qs_u32 kind, tl, lmask, pad;
+    qs_u64 gmask, gsel;
+};
+
+// U . exp(-i e/2 n.sigma) in FP64, split into float hi + lo.
+__device__ __forceinline__ void qs_noisy_matrix(const QsTrajOp &op, double e, float2 *u, float2 *ul) {
+    double r[8];
+    const double nx = op.ax[0], ny = op.ax[1], nz = op.ax[2];
+    if (nx == 0.0 && ny == 0.0 && nz == 0.0) {
+        for (int k = 0; k < 8; ++k) r[k] = op.U[k];
+    } else {
+        double sn, cs;
+        sincos(0.5 * e, &sn, &cs);
+        // E = c I - i s n.sigma = [[c - i s nz, -s ny - i s nx], [s ny - i s nx, c + i s nz]]
+        const double E[8] = {cs, -sn * nz, -sn * ny, -sn * nx, sn * ny, -sn * nx, cs, sn * nz};
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                double re = 0, im = 0;
+                for (int k = 0; k < 2; ++k) {
+                    const double ar = op.U[2 * (2 * i + k)], ai = op.U[2 * (2 * i + k) + 1];
+                    const double br = E[2 * (2 * k + j)], bi = E[2 * (2 * k + j) + 1];
+                    re += ar * br - ai * bi;
+                    im += ar * bi + ai * br;
+                }
+                r[2 * (2 * i + j)] = re;
+                r[2 * (2 * i + j) + 1] = im;
+            }
+    }
+    for (int k = 0; k < 4; ++k) {
+        const float hr = float(r[2 * k]), hi = float(r[2 * k + 1]);
+        u[k] = make_float2(hr, hi);
+        ul[k] = make_float2(float(r[2 * k] - double(hr)), float(r[2 * k + 1] - double(hi)));
+    }
+}

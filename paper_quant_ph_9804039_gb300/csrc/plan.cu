@@ -651,23 +651,30 @@ int find_swap_runs(const std::vector<Gate> &g, std::vector<int> &run_of, std::ve
 }
 
 // Shared-memory wavefronts of one warp access (lane byte addresses, `width`
-// bytes each): the largest number of distinct 4-byte words on one bank.
+// bytes each): the lanes are served in groups that move 128 bytes (32 lanes
+// of 4-byte, 16 of 8-byte, 8 of 16-byte accesses); within a group, the
+// largest number of distinct 4-byte words on one bank.
 int wavefronts(const uint32_t *addr, int width) {
-    uint32_t words[32][64];
-    int cnt[32] = {0};
-    int worst = 1;
-    for (int l = 0; l < 32; ++l)
-        for (int w = 0; w < width / 4; ++w) {
-            const uint32_t word = addr[l] / 4 + uint32_t(w);
-            const int bank = int(word & 31);
-            bool seen = false;
-            for (int i = 0; i < cnt[bank]; ++i) seen |= words[bank][i] == word;
-            if (!seen) {
-                words[bank][cnt[bank]++] = word;
-                worst = std::max(worst, cnt[bank]);
+    const int group = width >= 16 ? 8 : (width == 8 ? 16 : 32);
+    int total = 0;
+    for (int g0 = 0; g0 < 32; g0 += group) {
+        uint32_t words[32][64];
+        int cnt[32] = {0};
+        int worst = 1;
+        for (int l = g0; l < g0 + group; ++l)
+            for (int w = 0; w < width / 4; ++w) {
+                const uint32_t word = addr[l] / 4 + uint32_t(w);
+                const int bank = int(word & 31);
+                bool seen = false;
+                for (int i = 0; i < cnt[bank]; ++i) seen |= words[bank][i] == word;
+                if (!seen) {
+                    words[bank][cnt[bank]++] = word;
+                    worst = std::max(worst, cnt[bank]);
+                }
             }
-        }
-    return worst;
+        total += worst;
+    }
+    return total;
 }
 
 // Tile of the permutation pass: the lowest lb qubits (contiguous runs of
@@ -1150,6 +1157,16 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
 }
 
 }  // namespace
+
+namespace qs {
+
+bool build_register_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_count, TilePassDesc &d,
+                           int RB, std::vector<RegOp> &regops, std::vector<RoundDesc> &rounds,
+                           std::vector<unsigned char> &runs) {
+    return build_rounds(ops, op_begin, op_count, d, RB, regops, rounds, runs);
+}
+
+}  // namespace qs
 
 namespace qs {
 

@@ -188,12 +188,24 @@ struct RoundDesc {
 int launch_tile_reg(void *dst, const void *src, int M, const TilePassDesc &d, const void *ops_dev,
                     const void *rounds_dev, const void *runs_dev, cudaStream_t s);
 int tile_reg_prepare();
+// Group one tile pass's ops into register rounds of RB slot qubits (plan.cu):
+// appends to regops / rounds (and phase tables to runs); false if the pass
+// cannot use them.
+bool build_register_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_count, TilePassDesc &d,
+                           int RB, std::vector<RegOp> &regops, std::vector<RoundDesc> &rounds,
+                           std::vector<unsigned char> &runs);
 // Specialised register passes (jit.cu): generate, compile (NVRTC) and load one
 // kernel per pass; QSIM_EUNSUPPORTED (with *log) when NVRTC is unavailable.
 int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
               const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs, cudaLibrary_t *lib,
               std::vector<cudaKernel_t> *kernels, std::string *log);
 void jit_release(cudaLibrary_t lib);
+// The persistent trajectory kernel in register rounds ("qs_traj"): passes with
+// their rounds, op j of pass p = regops[passes[p].op_begin + j] whose gate is
+// trajectory op src[p][j]; __launch_bounds__(256, min_blocks).
+int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::vector<RegOp> &regops,
+                   const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks,
+                   cudaLibrary_t *lib, cudaKernel_t *kernel, std::string *log);
 int launch_jit_pass(cudaKernel_t k, void *dst, const void *src, int M, const TilePassDesc &d, const void *runs_dev,
                     cudaStream_t s);
 constexpr int kTileOpSmemBytes = 24 * 1024;  // a pass's ops are staged in shared memory up to this size

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "cx.cuh"
+#include "jit_device.cuh"
 #include "qsim_internal.h"
 #include "tile_ops.cuh"
 
@@ -47,40 +48,14 @@ struct TrajOp {
     uint64_t gsel;   // K_SCALE: the target bit (outside the tile)
 };
 
+static_assert(sizeof(TrajOp) == sizeof(QsTrajOp), "TrajOp and QsTrajOp share one layout");
 constexpr int kMaxPassOps = 256;  // gates per pass (matrices kept in shared memory)
 constexpr int kTrajThreads = 512;
 
-// U . exp(-i e/2 n.sigma) in FP64, split into float hi + lo.
-__device__ void noisy_matrix(const TrajOp &op, double e, float2 *u, float2 *ul) {
-    double r[8];
-    const double nx = op.ax[0], ny = op.ax[1], nz = op.ax[2];
-    if (nx == 0.0 && ny == 0.0 && nz == 0.0) {
-        for (int k = 0; k < 8; ++k) r[k] = op.U[k];
-    } else {
-        double sn, cs;
-        sincos(0.5 * e, &sn, &cs);
-        // E = c I - i s n.sigma = [[c - i s nz, -s ny - i s nx], [s ny - i s nx, c + i s nz]]
-        const double E[8] = {cs, -sn * nz, -sn * ny, -sn * nx, sn * ny, -sn * nx, cs, sn * nz};
-        for (int i = 0; i < 2; ++i)
-            for (int j = 0; j < 2; ++j) {
-                double re = 0, im = 0;
-                for (int k = 0; k < 2; ++k) {
-                    const double ar = op.U[2 * (2 * i + k)], ai = op.U[2 * (2 * i + k) + 1];
-                    const double br = E[2 * (2 * k + j)], bi = E[2 * (2 * k + j) + 1];
-                    re += ar * br - ai * bi;
-                    im += ar * bi + ai * br;
-                }
-                r[2 * (2 * i + j)] = re;
-                r[2 * (2 * i + j) + 1] = im;
-            }
-    }
-    for (int k = 0; k < 4; ++k) {
-        float hr, lr, hi, li;
-        split_f(r[2 * k], hr, lr);
-        split_f(r[2 * k + 1], hi, li);
-        u[k] = make_float2(hr, hi);
-        ul[k] = make_float2(lr, li);
-    }
+// U . exp(-i e/2 n.sigma) in FP64, split into float hi + lo (the same
+// function the specialised trajectory kernel compiles, jit_device.cuh).
+__device__ __forceinline__ void noisy_matrix(const TrajOp &op, double e, float2 *u, float2 *ul) {
+    qs_noisy_matrix(reinterpret_cast<const QsTrajOp &>(op), e, u, ul);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -218,6 +193,13 @@ struct qsim_traj_plan {
     int graph_T = -1;
     int use_graph = 0;
     size_t smem = 0;
+    // register-round kernel generated for the circuit (kernel_kind 2)
+    int kernel_kind = 1;  // 1: shared-memory tile kernel, 2: register rounds
+    int per_sm = 2;       // resident trajectories per SM (register kernel)
+    cudaLibrary_t jit_lib = nullptr;
+    cudaKernel_t jit_k = nullptr;
+    std::string log;      // why the register kernel could not be built
+    std::string tune;     // the autotuner's record
 };
 
 namespace {
@@ -225,7 +207,8 @@ namespace {
 // Tile passes over the error-free circuit's structure (the same greedy
 // grouping as the single-state passes; no phase runs, since every
 // trajectory's phases differ).
-int build_passes(qsim_traj_plan *p, const std::vector<Gate> &gates, const double *ax, int b_req) {
+int build_passes(qsim_traj_plan *p, const std::vector<Gate> &gates, const double *ax, int b_req,
+                 int max_ops = kMaxPassOps) {
     const int M = p->M;
     const int b = std::min(b_req, M);
     const int L = std::min(b, 5);
@@ -248,7 +231,7 @@ int build_passes(qsim_traj_plan *p, const std::vector<Gate> &gates, const double
             const Gate &g = gates[gi];
             const uint64_t N = nondiag(gi) ? bitq(g.t) : 0;
             const uint64_t A = bitq(g.t) | g.cmask;
-            bool ok = !((N & defA) || (A & defN)) && int(take.size()) < kMaxPassOps;
+            bool ok = !((N & defA) || (A & defN)) && int(take.size()) < max_ops;
             if (ok && nondiag(gi) && g.t >= L && !(high & bitq(g.t))) {
                 if (nh < cap) {
                     high |= bitq(g.t);
@@ -332,6 +315,20 @@ int upload_tables(qsim_traj_plan *p) {
 
 int launch_traj(qsim_traj_plan *p, int T) {
     QS_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), p->stream));
+    if (p->kernel_kind == 2) {
+        unsigned grid = unsigned(num_sms() * p->per_sm);
+        if (grid > unsigned(p->grid)) grid = unsigned(p->grid);
+        const TrajOp *ops = p->d_ops;
+        const double *eps = p->d_eps;
+        int n = p->n;
+        const float2 *ideal = p->d_ideal;
+        float2 *work = p->d_work;
+        double *F = p->d_F;
+        unsigned *counter = p->d_counter;
+        void *args[] = {&ops, &eps, &n, &T, &ideal, &work, &F, &counter};
+        QS_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(p->jit_k), dim3(grid), dim3(256), args, 0, p->stream));
+        return QSIM_OK;
+    }
     k_trajectories<<<p->grid, kTrajThreads, p->smem, p->stream>>>(p->M, int(p->passes.size()), p->d_passes, p->d_ops,
                                                                   p->d_eps, p->n, T, p->d_ideal, p->d_work, p->d_F,
                                                                   p->d_counter);
@@ -339,7 +336,57 @@ int launch_traj(qsim_traj_plan *p, int T) {
     return QSIM_OK;
 }
 
+// The register-round kernel for tiles of 2^b amplitudes (b = 11 or 12: 3 or
+// 4 register qubits per thread): the tile passes of build_passes, each split
+// into rounds by build_rounds, generated and compiled as one persistent
+// kernel.  Each op carries its trajectory op's index through the rounds in a
+// placeholder matrix entry (the kernel takes its matrices from shared memory).
+int build_register_kernel(qsim_traj_plan *p, const std::vector<Gate> &gates, const double *ax, int b) {
+    if (p->jit_lib) jit_release(p->jit_lib);
+    p->jit_lib = nullptr;
+    p->jit_k = nullptr;
+    p->kernel_kind = 1;
+    if (p->M < b) return QSIM_EUNSUPPORTED;
+    p->tile_bits = b;
+    if (int rc = build_passes(p, gates, ax, b, 150)) return rc;
+    if (int rc = upload_tables(p)) return rc;
+    const int RB = b - kRegThreadBits;
+    std::vector<TilePassDesc> passes;
+    std::vector<RegOp> regops;
+    std::vector<RoundDesc> rounds;
+    std::vector<unsigned char> runs(16, 0);
+    std::vector<std::vector<int>> src;
+    for (const TilePassDesc &d0 : p->passes) {
+        if (d0.b != b) return QSIM_EUNSUPPORTED;
+        std::vector<TileOp<float2>> tops(size_t(d0.op_count));
+        for (int j = 0; j < d0.op_count; ++j) {
+            const TrajOp &op = p->ops[size_t(d0.op_begin + j)];
+            TileOp<float2> &t = tops[size_t(j)];
+            t.kind = op.kind;
+            t.tl = op.tl;
+            t.lmask = op.lmask;
+            t.gmask = op.gmask;
+            t.gsel = op.gsel;
+            for (int k = 0; k < 4; ++k) t.u[k] = make_float2(1.f, 0.5f);  // complex: no real-entry forms
+            t.u[0].x = float(d0.op_begin + j);                             // the trajectory op (exact below 2^24)
+        }
+        TilePassDesc d = d0;
+        if (!build_register_rounds(tops, 0, d0.op_count, d, RB, regops, rounds, runs)) return QSIM_EUNSUPPORTED;
+        std::vector<int> s(size_t(d.op_count));
+        for (int j = 0; j < d.op_count; ++j) s[size_t(j)] = int(regops[size_t(d.op_begin + j)].u[0].x);
+        passes.push_back(d);
+        src.push_back(s);
+    }
+    if (int rc = jit_build_traj(p->M, passes, regops, rounds, src, 2, &p->jit_lib, &p->jit_k, &p->log)) return rc;
+    p->kernel_kind = 2;
+    return QSIM_OK;
+}
+
 int set_tile_bits(qsim_traj_plan *p, const std::vector<Gate> &gates, const double *ax, int b) {
+    if (p->jit_lib) jit_release(p->jit_lib);
+    p->jit_lib = nullptr;
+    p->jit_k = nullptr;
+    p->kernel_kind = 1;
     p->tile_bits = std::min(b, p->M);
     if (int rc = build_passes(p, gates, ax, p->tile_bits)) return rc;
     if (int rc = upload_tables(p)) return rc;
@@ -364,6 +411,7 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
     qsim_traj_opts o{};
     if (opts) o = *opts;
     if (o.fuse_k < 0 || o.fuse_k > 5) { set_error("fuse_k %d outside [0, 5]", o.fuse_k); return QSIM_EINVAL; }
+    if (o.kernel < 0 || o.kernel > 2) { set_error("kernel %d outside [0, 2]", o.kernel); return QSIM_EINVAL; }
     std::vector<Gate> gates(n);
     for (size_t i = 0; i < n; ++i) {
         if (int rc = make_gate(M, ideal[i].U, ideal[i].target, ideal[i].controls, ideal[i].ncontrols, &gates[i])) {
@@ -423,6 +471,18 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
         key.push_back(ideal[i].controls[1]);
         key.insert(key.end(), err_axis + 3 * i, err_axis + 3 * i + 3);
     }
+    // configuration code: b (10..13) the shared-memory tile kernel with tiles
+    // of 2^b; 100 + 10 b + s the register-round kernel with tiles of 2^b
+    // (b - 8 register qubits per thread) and s resident trajectories per SM
+    key.push_back(o.kernel);
+    auto apply = [&](int code) -> int {
+        if (code < 100) return set_tile_bits(p, gates, err_axis, code);
+        const int b = (code - 100) / 10;
+        if (p->kernel_kind != 2 || p->tile_bits != b)
+            if (int r = build_register_kernel(p, gates, err_axis, b)) return r;
+        p->per_sm = code % 10;
+        return QSIM_OK;
+    };
     int best = 0;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -430,16 +490,32 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
         if (it != g_tune_cache.end()) best = it->second;
     }
     if (best == 0) {
-        const int cands[] = {10, 11, 12, 13};
+        std::vector<int> cands;
+        if (o.kernel != 2)
+            for (int b : {10, 11, 12, 13})
+                if (b <= M || b == 10) cands.push_back(b);
+        if (o.kernel != 1)
+            for (int b : {11, 12})
+                if (b <= M)
+                    for (int s : {1, 2}) cands.push_back(100 + 10 * b + s);
+        if (cands.empty()) cands.push_back(10);
         float best_ms = 1e30f;
         const int Tt = std::min(max_T, p->grid);
         cudaMemsetAsync(p->d_eps, 0, size_t(Tt) * std::max<size_t>(n, 1) * sizeof(double), p->stream);
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int b : cands) {
-            if (b > M && b != cands[0]) continue;
-            if ((rc = set_tile_bits(p, gates, err_axis, b))) break;
+        char line[256];
+        for (int code : cands) {
+            const int arc = apply(code);
+            if (arc == QSIM_EUNSUPPORTED) {  // no NVRTC, or a pass too large for register rounds
+                snprintf(line, sizeof line, "register kernel, tiles 2^%d: unavailable (%s)\n", (code - 100) / 10,
+                         p->log.empty() ? "pass structure" : p->log.c_str());
+                p->log.clear();
+                p->tune += line;
+                continue;
+            }
+            if ((rc = arc)) break;
             float ms = 0.f;
             for (int rep = 0; rep < 2 && rc == QSIM_OK; ++rep) {
                 cudaEventRecord(e0, p->stream);
@@ -450,18 +526,35 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
                 cudaEventElapsedTime(&ms, e0, e1);
             }
             if (rc) break;
+            if (code < 100)
+                snprintf(line, sizeof line, "shared-memory kernel, tiles 2^%d: %.3f ms for %d trajectories\n", code, ms,
+                         Tt);
+            else
+                snprintf(line, sizeof line,
+                         "register kernel, tiles 2^%d, %d register qubits, %d per SM: %.3f ms for %d trajectories\n",
+                         (code - 100) / 10, (code - 100) / 10 - kRegThreadBits, code % 10, ms, Tt);
+            p->tune += line;
             if (ms < best_ms) {
                 best_ms = ms;
-                best = std::min(b, M);
+                best = code;
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (rc) return fail(rc);
+        if (best == 0) best = 10;
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    if ((rc = set_tile_bits(p, gates, err_axis, best))) return fail(rc);
+    if ((rc = apply(best)) == QSIM_EUNSUPPORTED) rc = apply(12);
+    if (rc) return fail(rc);
+    {
+        char line[160];
+        snprintf(line, sizeof line, "chosen: %s, tiles 2^%d%s\n",
+                 p->kernel_kind == 2 ? "register-round kernel" : "shared-memory tile kernel", p->tile_bits,
+                 p->kernel_kind == 2 ? (p->per_sm == 1 ? ", 1 per SM" : ", 2 per SM") : "");
+        p->tune += line;
+    }
     *out = p;
     return QSIM_OK;
 }
@@ -520,9 +613,22 @@ int qsim_traj_plan_info(const qsim_traj_plan *p, int *tile_bits, int *n_passes, 
     return QSIM_OK;
 }
 
+int qsim_traj_plan_describe(const qsim_traj_plan *p, char *buf, int64_t len, int64_t *needed) {
+    if (!p) { set_error("plan is NULL"); return QSIM_EINVAL; }
+    if (len > 0 && !buf) { set_error("buf is NULL"); return QSIM_EINVAL; }
+    if (needed) *needed = int64_t(p->tune.size()) + 1;
+    if (len > 0) {
+        const size_t k = std::min(p->tune.size(), size_t(len - 1));
+        std::memcpy(buf, p->tune.data(), k);
+        buf[k] = 0;
+    }
+    return QSIM_OK;
+}
+
 void qsim_traj_plan_destroy(qsim_traj_plan *p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
+    jit_release(p->jit_lib);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     cudaFree(p->d_passes);
     cudaFree(p->d_ops);

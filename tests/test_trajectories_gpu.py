@@ -84,3 +84,44 @@ def test_batched_brickwork_m16_t4096(orc):
     assert np.abs(F - Fo).max() <= DF
     assert abs(mean - mo) <= DF and abs(var - vo) <= _var_tol(vo, len(F))
     assert 0.5 < mean < 1.0 and plan.info()["n_passes"] >= 1
+
+
+def _diag_circuit(M, rng):
+    """Hadamards, controlled phases and Rz gates with z-axis errors (diagonal
+    erroneous gates: inside the tile and on outside qubits), plus Haar gates."""
+    recs, axes = [], []
+    for layer in range(4):
+        for q in range(M):
+            recs.append(W.gate_record(W.mat_h() if layer % 2 == 0 else W.mat_haar_su2(rng), q))
+            axes.append(list(W.su2_axis(W.record_matrix(recs[-1]))[1]) if layer % 2 else [1.0, 0.0, 0.0])
+        for _ in range(2 * M):
+            t = int(rng.integers(M))
+            c = int(rng.choice([v for v in range(M) if v != t]))
+            if rng.random() < 0.5:
+                recs.append(W.gate_record(W.mat_phase(float(rng.uniform(-3, 3))), t, (c,)))
+            else:
+                recs.append(W.gate_record(W.mat_rz(float(rng.uniform(-3, 3))), t))
+            axes.append([0.0, 0.0, 1.0])
+    return W._pack(recs), np.array(axes, dtype=np.float64)
+
+
+@pytest.mark.parametrize("kernel", ["smem", "register"])
+@pytest.mark.parametrize("M,layers,T,case", [(11, 5, 40, "brick"), (13, 6, 64, "brick"), (16, 4, 50, "brick"),
+                                              (12, 0, 30, "diag"), (14, 0, 30, "diag")])
+def test_trajectory_kernels_match_oracle(orc, kernel, M, layers, T, case):
+    """Both trajectory kernels (shared-memory tile passes; register rounds
+    generated for the circuit) against the oracle, trajectory by trajectory."""
+    rng = np.random.default_rng(800 + M)
+    if case == "brick":
+        b = W.circuit_brickwork(M, layers, toffoli_every=2)
+        gates, axes = b["ideal"], b["axes"]
+    else:
+        gates, axes = _diag_circuit(M, rng)
+    eps = W.trajectory_eps(len(gates), T, 5e-3)
+    plan = qs.TrajPlan(M, gates, axes, max_T=T, kernel=kernel)
+    d = plan.describe()
+    assert ("chosen: register-round kernel" in d) == (kernel == "register"), d
+    F, mean, var = plan.run(eps)
+    Fo, mo, vo = orc.trajectories(M, gates, axes, eps, nthreads=NT)
+    assert np.abs(F - Fo).max() <= DF
+    assert abs(mean - mo) <= DF and abs(var - vo) <= _var_tol(vo, len(F))
