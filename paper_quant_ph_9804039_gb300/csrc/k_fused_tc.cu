@@ -35,24 +35,28 @@
 // (cp.async) by all lanes of the producer warp: bulk copies of the 1 KiB runs
 // of a tile on high qubits were measured at half the bandwidth.
 //
-// Per CTA (persistent over tiles, one per SM, 320 threads), warp-specialised
+// Per CTA (persistent over tiles, one per SM, 384 threads), warp-specialised
 // and pipelined over tiles:
-//   warp 0       producer: asynchronous copies of a tile into one of 3 input
-//                stages, each lane arriving on the stage's mbarrier when its
-//                copies have landed;
-//   warp 1       MMA: 12 tcgen05.mma per tile (3 products x row blocks x
+//   warps 0..2   producers: asynchronous copies of a tile into one of 3 or 4
+//                input stages, each lane arriving on the stage's mbarrier
+//                when its copies have landed;
+//   warp 3       MMA: 12 tcgen05.mma per tile (3 products x row blocks x
 //                K steps of 16) into one of 2 TMEM accumulators (64 columns
 //                each), committed to mbarriers;
-//   warps 2..5   split: each thread owns one sub-vector row per row block,
+//   warps 4..7   split: each thread owns one sub-vector row per row block,
 //                reads its 2^k amplitudes (in a lane-skewed order, so the
 //                warp's reads and writes fall on distinct banks), scales,
 //                splits and writes X_hi, X_lo into one of 2 operand stages in
 //                the canonical K-major swizzled layout the MMA reads;
-//   warps 6..9   epilogue: each thread reads its row of the accumulator
-//                (tcgen05.ld), removes the scale, renormalises, writes the
-//                amplitudes into an XOR-swizzled staging tile, and the four
-//                warps then copy the staging tile to device memory in
-//                coalesced runs (8 loads in flight per thread).
+//   warps 8..11  epilogue: each thread reads its row of the accumulator
+//                (tcgen05.ld), removes the scale, renormalises and stores
+//                the amplitudes: straight to device memory when the 32 rows
+//                of a warp are 32 consecutive amplitudes (the block avoids
+//                qubits 0..4; then a fourth input stage takes the staging
+//                tile's shared memory), otherwise into an XOR-swizzled
+//                staging tile that the four warps copy out in coalesced runs.
+// The split warps release an input stage as soon as the tile is in their
+// registers, before converting it.
 // Every mbarrier wait is bounded (2 s of globaltimer); on a timeout the CTA
 // records QSIM_ETIMEOUT in the status word, the other roles leave their loops,
 // the producer waits (bounded) for its copies in flight, the MMA warp for its
@@ -65,8 +69,12 @@
 namespace qs {
 namespace {
 
-constexpr int kThreads = 320;  // 10 warps
-constexpr int kNIn = 3;        // input stages
+constexpr int kProd = 3;                    // producer warps (one per scheduler, 0..2)
+constexpr int kMmaWarp = kProd;             // the MMA warp
+constexpr int kSplit0 = kProd + 1;          // first of the 4 split warps
+constexpr int kEpi0 = kProd + 5;            // first of the 4 epilogue warps
+constexpr int kThreads = 32 * (kProd + 9);  // 12 warps
+constexpr int kMaxIn = 4;      // input stages (3 with a staging tile for the output, 4 without)
 constexpr int kNA = 2;         // operand stages = accumulator stages
 constexpr int kTileAmps = 1 << kFusedTileBits;
 constexpr uint32_t kInBytes = kTileAmps * 8;
@@ -209,8 +217,9 @@ __device__ __forceinline__ void tmem_wait_ld(float *v) {
                      "+f"(v[i + 6]), "+f"(v[i + 7]));
 }
 
-template <int KF>
+template <int KF, bool DIRECT>
 struct Cfg {
+    static constexpr int NIN = DIRECT ? 4 : 3;         // input stages
     static constexpr int NA = 1 << KF;                 // amplitudes per sub-vector
     static constexpr int KR = 2 * NA;                  // reals per sub-vector (MMA K and N)
     static constexpr int W = KR * 2;                   // bytes of one operand row (FP16)
@@ -221,20 +230,21 @@ struct Cfg {
     static constexpr int KSTEPS = KR / 16;             // MMA K = 16 (32 bytes)
     // dynamic shared memory: inputs, operands (hi, lo per stage), R, staging
     static constexpr uint32_t OFF_IN = 0;
-    static constexpr uint32_t OFF_A = OFF_IN + kNIn * kInBytes;
+    static constexpr uint32_t OFF_A = OFF_IN + NIN * kInBytes;
     static constexpr uint32_t OFF_B = OFF_A + kNA * 2 * kABytes;
     static constexpr uint32_t OFF_OUT = OFF_B + 2 * (B_BYTES < 1024 ? 1024 : B_BYTES);
-    static constexpr uint32_t SMEM = 1024 + OFF_OUT + kInBytes;
+    static constexpr uint32_t SMEM = 1024 + OFF_OUT + (DIRECT ? 0 : kInBytes);
 };
 
 struct SmemCtl {
-    uint64_t full_in[kNIn], empty_in[kNIn];
+    uint64_t full_in[kMaxIn], empty_in[kMaxIn];
     uint64_t full_a[kNA], empty_a[kNA];
     uint64_t full_acc[kNA], empty_acc[kNA];
     uint64_t bar_r;
     uint64_t epi_full, epi_free;          // staging tile written / copied out (4 epilogue warps)
     uint64_t runoff[32];                  // device offset of run r of a tile (tile 0)
     uint64_t runoff2[32];                 // device offset of tile-local index 128 j (tile 0)
+    uint64_t gA[32];                      // device offset of combination a (sub-vector 0, tile 0)
     uint32_t tmem;
     int abort;
     uint32_t swA8[32];                    // 8 * swz(posA[a]): staging byte offset of combination a
@@ -245,11 +255,12 @@ struct SmemCtl {
 // XOR swizzle of the staging tile (8-byte amplitudes): bits [0,4) ^= bits [r, r+4).
 __device__ __forceinline__ uint32_t stg_swz(uint32_t u, int r) { return u ^ ((u >> r) & 15u); }
 
-template <int KF>
+template <int KF, bool DIRECT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_tc(float2 *dst, const float2 *src, FusedDesc d, const __half *__restrict__ rimg, uint64_t ntiles,
                int *status) {
-    using C = Cfg<KF>;
+    using C = Cfg<KF, DIRECT>;
+    constexpr int kNIn = C::NIN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // 1024-byte aligned, derived from the shared array by pointer arithmetic so
     // that every access through it stays a shared-memory access (no aliasing
@@ -264,6 +275,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int m = tid; m < C::NROWS; m += kThreads) ctl.posM[m] = d.posM[m];
     if (tid < C::NA) ctl.swA8[tid] = 8u * stg_swz(d.posA[tid], d.outsh);
     if (tid < 32) ctl.runoff2[tid] = d.runoff2[tid];
+    if (tid < C::NA) {  // tile-local index posA[a] -> device offset
+        const uint32_t u = d.posA[tid];
+        uint64_t off = u & (run_amps - 1);
+        for (int b = 0; b < d.nrb; ++b)
+            if (((u >> d.runbits) >> b) & 1) off |= uint64_t(1) << d.rpos[b];
+        ctl.gA[tid] = off;
+    }
     if (tid < nrun) {
         uint64_t off = 0;
         for (int b = 0; b < d.nrb; ++b)
@@ -272,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (tid == 0) {
         for (int b = 0; b < kNIn; ++b) {
-            mbar_init(&ctl.full_in[b], 32);
+            mbar_init(&ctl.full_in[b], 32 * kProd);
             mbar_init(&ctl.empty_in[b], 4);
         }
         for (int b = 0; b < kNA; ++b) {
@@ -287,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ctl.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(&ctl.tmem, kTmemCols);
+    if (warp == kMmaWarp) tmem_alloc(&ctl.tmem, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -305,12 +323,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     bool ok = true;
 
-    if (warp == 0) {
+    if (warp < kProd) {
         // ------------------------------------------------------------ producer
-        // all 32 lanes copy the tile in 16-byte pieces (cp.async), each lane
-        // arriving on the stage's barrier once its copies have landed
+        // the producer warps (one per scheduler) copy the tile in 16-byte
+        // pieces (cp.async), each lane arriving on the stage's barrier once its
+        // copies have landed
         uint64_t issued = 0;
-        if (lane == 0) {
+        const int ptid = warp * 32 + lane;
+        if (warp == 0 && lane == 0) {
             unsigned char *Bs = sm + C::OFF_B;
             const uint32_t bstride = C::B_BYTES < 1024 ? 1024 : C::B_BYTES;
             mbar_expect_tx(&ctl.bar_r, 2 * C::B_BYTES);
@@ -326,9 +346,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const uint64_t base = tile_base(i);
             unsigned char *buf = sm + C::OFF_IN + size_t(s) * kInBytes;
-#pragma unroll 8
-            for (int c = 0; c < kTileAmps / 2 / 32; ++c) {
-                const uint32_t u = 2u * (uint32_t(c) * 32u + uint32_t(lane));
+#pragma unroll 4
+            for (int c = ptid; c < kTileAmps / 2; c += 32 * kProd) {
+                const uint32_t u = 2u * uint32_t(c);
                 cp_async16(buf + 8u * u, src + base + ctl.runoff[u >> d.runbits] + (u & rmask));
             }
             cp_async_arrive(&ctl.full_in[s]);
@@ -339,14 +359,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) atomicExch(status, QSIM_ETIMEOUT);
             ctl.abort = 1;
         }
-        if (lane == 0) {
+        if (warp == 0 && lane == 0) {
             const uint64_t t0 = globaltimer();
             while (!mbar_try_wait(&ctl.bar_r, 0))
                 if (globaltimer() - t0 > kWaitNs) break;
         }
         (void)issued;
         __syncwarp();
-    } else if (warp == 1) {
+    } else if (warp == kMmaWarp) {
         // ----------------------------------------------------------------- MMA
         uint64_t done = 0;  // tiles whose MMAs were issued
         if (lane == 0) {
@@ -392,9 +412,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
-    } else if (warp < 6) {
+    } else if (warp < kEpi0) {
         // --------------------------------------------------------------- split
-        const int sw = warp - 2;
+        const int sw = warp - kSplit0;
         const uint32_t g = d.skew[lane];
         const uint32_t pAg = d.posA[g];
         uint32_t posA8[C::NA];
@@ -420,6 +440,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int s = 0; s < C::NA; ++s) {
                     x[s] = *reinterpret_cast<const float2 *>(in + (posA8[s] ^ lin));
                     mx = fmaxf(mx, fmaxf(fabsf(x[s].x), fabsf(x[s].y)));
+                }
+                if (rb + 1 == C::NRB) {  // the tile is in registers: its input stage can be refilled
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ctl.empty_in[s_in]);
                 }
                 // scale 2^es puts the largest component in [2^14, 2^15); rows below
                 // 2^-104 keep es = 118, so that 2^-es-8 stays a normal float
@@ -449,8 +473,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 ctl.rowinfo[t][m] = make_float2(sx, inv);
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl.empty_in[s_in]);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl.full_a[t]);
@@ -462,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------------------ epilogue
         const int qd = warp & 3;  // TMEM lane quadrant of this warp
-        const int te = tid - 6 * 32;  // 0..127
+        const int te = tid - kEpi0 * 32;  // 0..127
         const unsigned char *outb = sm + C::OFF_OUT;
         for (uint64_t i = 0; i < n_local; ++i) {
             const int t = int(i % kNA);
@@ -502,11 +524,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int j = 0; j < C::KR; ++j) y[rb][j] = fmaf(y[rb][j], c, y[rb][j]);
                 }
             }
+            const uint64_t base = tile_base(i);
+            if constexpr (DIRECT) {
+                // the 32 rows of a warp are 32 consecutive amplitudes: every store
+                // of a combination a writes 256 contiguous bytes, no staging
+#pragma unroll
+                for (int rb = 0; rb < C::NRB; ++rb) {
+                    const uint32_t u = ctl.posM[rb * 128 + rho];
+                    float2 *drow = dst + base + (ctl.runoff[u >> d.runbits] | (u & (run_amps - 1)));
+#pragma unroll
+                    for (int a = 0; a < C::NA; ++a) drow[ctl.gA[a]] = make_float2(y[rb][2 * a], y[rb][2 * a + 1]);
+                }
+                continue;
+            }
             if (i > 0 && !warp_wait(&ctl.epi_free, uint32_t((i - 1) & 1), abort)) {  // staging copied out
                 ok = false;
                 break;
             }
-            const uint64_t base = tile_base(i);
 #pragma unroll
             for (int rb = 0; rb < C::NRB; ++rb) {
                 const uint32_t swm = 8u * stg_swz(ctl.posM[rb * 128 + rho], d.outsh);
@@ -544,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+    if (warp == kMmaWarp) tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace
@@ -554,9 +588,15 @@ int fused_prepare() {
     int dev = 0;
     QS_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && configured[dev]) return QSIM_OK;
-    QS_CUDA(cudaFuncSetAttribute(k_fused_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<3>::SMEM)));
-    QS_CUDA(cudaFuncSetAttribute(k_fused_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<4>::SMEM)));
-    QS_CUDA(cudaFuncSetAttribute(k_fused_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<5>::SMEM)));
+#define QS_FUSED_ATTR(K, D) \
+    QS_CUDA(cudaFuncSetAttribute(k_fused_tc<K, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<K, D>::SMEM)))
+    QS_FUSED_ATTR(3, false);
+    QS_FUSED_ATTR(4, false);
+    QS_FUSED_ATTR(5, false);
+    QS_FUSED_ATTR(3, true);
+    QS_FUSED_ATTR(4, true);
+    QS_FUSED_ATTR(5, true);
+#undef QS_FUSED_ATTR
     if (dev < 64) configured[dev] = 1;
     return QSIM_OK;
 }
@@ -572,12 +612,18 @@ int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const vo
     float2 *o = static_cast<float2 *>(dst);
     const float2 *i = static_cast<const float2 *>(src);
     const __half *r = static_cast<const __half *>(rimg_dev);
-    switch (d.k) {
-        case 3: k_fused_tc<3><<<unsigned(grid), kThreads, Cfg<3>::SMEM, s>>>(o, i, d, r, ntiles, status); break;
-        case 4: k_fused_tc<4><<<unsigned(grid), kThreads, Cfg<4>::SMEM, s>>>(o, i, d, r, ntiles, status); break;
-        case 5: k_fused_tc<5><<<unsigned(grid), kThreads, Cfg<5>::SMEM, s>>>(o, i, d, r, ntiles, status); break;
+#define QS_FUSED_LAUNCH(K, D) \
+    k_fused_tc<K, D><<<unsigned(grid), kThreads, Cfg<K, D>::SMEM, s>>>(o, i, d, r, ntiles, status)
+    switch (d.k * 2 + (d.direct ? 1 : 0)) {
+        case 6: QS_FUSED_LAUNCH(3, false); break;
+        case 7: QS_FUSED_LAUNCH(3, true); break;
+        case 8: QS_FUSED_LAUNCH(4, false); break;
+        case 9: QS_FUSED_LAUNCH(4, true); break;
+        case 10: QS_FUSED_LAUNCH(5, false); break;
+        case 11: QS_FUSED_LAUNCH(5, true); break;
         default: set_error("fused block width %d outside [3, 5]", d.k); return QSIM_EINVAL;
     }
+#undef QS_FUSED_LAUNCH
     QS_CHECK_LAUNCH("fused tensor-core launch");
     return QSIM_OK;
 }

@@ -988,6 +988,8 @@ FusedDesc fused_desc(int M, int k, const int *bq) {
             if ((m >> j) & 1) u |= 1u << idx[fq[j]];
         d.posM[m] = uint16_t(u);
     }
+    d.direct = 1;
+    for (int m = 0; m < 32 && m < NROWS; ++m) d.direct &= d.posM[m] == m ? 1 : 0;
     for (int j = 0; j < 32; ++j) {
         const uint32_t u = uint32_t(j) << 7;
         uint64_t off = 0;

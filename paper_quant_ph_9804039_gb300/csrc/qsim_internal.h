@@ -230,6 +230,7 @@ struct FusedDesc {
     int nout;                    // qubits outside the tile (number the tiles)
     int opos[QSIM_MAX_QUBITS];
     int outsh;                   // staging swizzle: bits [0,4) of the tile index ^= bits [outsh, outsh+4)
+    int direct;                  // sub-vectors 0..31 are amplitudes 0..31 of the tile: store without staging
     uint16_t posA[32];           // u of block combination a (sub-vector 0)
     uint16_t posM[1 << kFusedRowBits];  // u of sub-vector m (combination 0)
     uint8_t skew[32];            // split: lane l visits combination s ^ skew[l] at step s
