@@ -19,7 +19,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -390,50 +393,71 @@ std::string emit_traj(int M, const std::vector<TilePassDesc> &passes, const std:
     return out.s;
 }
 
-}  // namespace
-
-int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
-              const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs, cudaLibrary_t *lib,
-              std::vector<cudaKernel_t> *kernels, std::string *log) {
+// Compile one program for sm_103a; false (and *log) on failure.
+bool compile_cubin(const std::string &src, const char *name, std::vector<char> *cubin, std::string *log) {
     Nvrtc &n = nvrtc();
-    if (!n.ok) {
-        if (log) *log = "NVRTC not found";
-        return QSIM_EUNSUPPORTED;
-    }
-    std::string src = kJitHeader;
-    for (size_t i = 0; i < passes.size(); ++i) src += emit_pass(int(i), *passes[i], regops, rounds, runs);
     nvrtcProgram prog;
-    if (n.create(&prog, src.c_str(), "qsim_passes.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
-        if (log) *log = "nvrtcCreateProgram failed";
-        return QSIM_EUNSUPPORTED;
+    if (n.create(&prog, src.c_str(), name, 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        *log = "nvrtcCreateProgram failed";
+        return false;
     }
     const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17"};
-    const nvrtcResult rc = n.compile(prog, 2, opts);
-    if (rc != NVRTC_SUCCESS) {
+    if (n.compile(prog, 2, opts) != NVRTC_SUCCESS) {
         size_t ls = 0;
         n.log_size(prog, &ls);
         std::string l(ls, '\0');
         if (ls) n.log(prog, &l[0]);
-        if (log) *log = "NVRTC compilation failed: " + l.substr(0, 2000);
+        *log = "NVRTC compilation failed: " + l.substr(0, 2000);
         n.destroy(&prog);
-        return QSIM_EUNSUPPORTED;
+        return false;
     }
     size_t cs = 0;
     n.cubin_size(prog, &cs);
-    std::vector<char> cubin(cs);
-    n.cubin(prog, cubin.data());
+    cubin->resize(cs);
+    n.cubin(prog, cubin->data());
     n.destroy(&prog);
-    cudaError_t e = cudaLibraryLoadData(lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "loading the specialised passes");
-    kernels->assign(passes.size(), nullptr);
-    for (size_t i = 0; i < passes.size(); ++i) {
-        char name[32];
-        std::snprintf(name, sizeof name, "qs_pass_%zu", i);
-        e = cudaLibraryGetKernel(&(*kernels)[i], *lib, name);
+    return true;
+}
+
+}  // namespace
+
+// One program per pass, compiled on a pool of host threads (compile time
+// grows faster than linearly with the program, and passes are independent),
+// each loaded as its own library.
+int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
+              const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs,
+              std::vector<cudaLibrary_t> *libs, std::vector<cudaKernel_t> *kernels, std::string *log) {
+    if (!nvrtc().ok) {
+        if (log) *log = "NVRTC not found";
+        return QSIM_EUNSUPPORTED;
+    }
+    const size_t np = passes.size();
+    std::vector<std::string> srcs(np), logs(np);
+    for (size_t i = 0; i < np; ++i) srcs[i] = std::string(kJitHeader) + emit_pass(0, *passes[i], regops, rounds, runs);
+    std::vector<std::vector<char>> cubins(np);
+    std::vector<char> ok(np, 0);
+    std::atomic<size_t> next{0};
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (unsigned w = 0; w < std::min<unsigned>(hw, unsigned(np)); ++w)
+        pool.emplace_back([&]() {
+            for (size_t i; (i = next.fetch_add(1)) < np;) ok[i] = compile_cubin(srcs[i], "qsim_pass.cu", &cubins[i], &logs[i]);
+        });
+    for (std::thread &t : pool) t.join();
+    for (size_t i = 0; i < np; ++i)
+        if (!ok[i]) {
+            if (log) *log = logs[i];
+            return QSIM_EUNSUPPORTED;
+        }
+    libs->assign(np, nullptr);
+    kernels->assign(np, nullptr);
+    for (size_t i = 0; i < np; ++i) {
+        cudaError_t e = cudaLibraryLoadData(&(*libs)[i], cubins[i].data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+        if (e == cudaSuccess) e = cudaLibraryGetKernel(&(*kernels)[i], (*libs)[i], "qs_pass_0");
         if (e != cudaSuccess) {
-            cudaLibraryUnload(*lib);
-            *lib = nullptr;
-            return cuda_fail(e, "finding a specialised pass");
+            jit_release(*libs);
+            libs->clear();
+            return cuda_fail(e, "loading a specialised pass");
         }
     }
     return QSIM_OK;
@@ -442,32 +466,17 @@ int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector
 int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::vector<RegOp> &regops,
                    const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks,
                    cudaLibrary_t *lib, cudaKernel_t *kernel, std::string *log) {
-    Nvrtc &n = nvrtc();
-    if (!n.ok) {
+    if (!nvrtc().ok) {
         if (log) *log = "NVRTC not found";
         return QSIM_EUNSUPPORTED;
     }
-    const std::string src_text = std::string(kJitHeader) + emit_traj(M, passes, regops, rounds, src, min_blocks);
-    nvrtcProgram prog;
-    if (n.create(&prog, src_text.c_str(), "qsim_traj.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
-        if (log) *log = "nvrtcCreateProgram failed";
+    const std::string text = std::string(kJitHeader) + emit_traj(M, passes, regops, rounds, src, min_blocks);
+    std::vector<char> cubin;
+    std::string l;
+    if (!compile_cubin(text, "qsim_traj.cu", &cubin, &l)) {
+        if (log) *log = l;
         return QSIM_EUNSUPPORTED;
     }
-    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17"};
-    if (n.compile(prog, 2, opts) != NVRTC_SUCCESS) {
-        size_t ls = 0;
-        n.log_size(prog, &ls);
-        std::string l(ls, '\0');
-        if (ls) n.log(prog, &l[0]);
-        if (log) *log = "NVRTC compilation failed: " + l.substr(0, 2000);
-        n.destroy(&prog);
-        return QSIM_EUNSUPPORTED;
-    }
-    size_t cs = 0;
-    n.cubin_size(prog, &cs);
-    std::vector<char> cubin(cs);
-    n.cubin(prog, cubin.data());
-    n.destroy(&prog);
     cudaError_t e = cudaLibraryLoadData(lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e != cudaSuccess) return cuda_fail(e, "loading the trajectory kernel");
     e = cudaLibraryGetKernel(kernel, *lib, "qs_traj");
@@ -481,6 +490,10 @@ int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::ve
 
 void jit_release(cudaLibrary_t lib) {
     if (lib) cudaLibraryUnload(lib);
+}
+
+void jit_release(const std::vector<cudaLibrary_t> &libs) {
+    for (cudaLibrary_t l : libs) jit_release(l);
 }
 
 int launch_jit_pass(cudaKernel_t k, void *dst, const void *src, int M, const TilePassDesc &d, const void *runs_dev,

@@ -57,7 +57,7 @@ struct qsim_plan {
     std::vector<RegOp> h_regops;  // host copies, for qsim_plan_describe
     std::vector<RoundDesc> h_rounds;
     // specialised register passes (qsim_opts.specialize): one kernel per step, or null
-    cudaLibrary_t jit_lib = nullptr;
+    std::vector<cudaLibrary_t> jit_libs;
     std::vector<cudaKernel_t> jit_k;
     std::string jit_log;
     int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
@@ -1302,7 +1302,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
                             at.push_back(si);
                         }
                     std::vector<cudaKernel_t> ks;
-                    if (!descs.empty() && jit_build(descs, regops, rounds, runs, &p->jit_lib, &ks, &p->jit_log) == QSIM_OK) {
+                    if (!descs.empty() && jit_build(descs, regops, rounds, runs, &p->jit_libs, &ks, &p->jit_log) == QSIM_OK) {
                         p->jit_k.assign(p->steps.size(), nullptr);
                         for (size_t j = 0; j < at.size(); ++j) p->jit_k[at[j]] = ks[j];
                     }
@@ -1346,8 +1346,8 @@ void plan_release(qsim_plan *p) {
     dev_free(p, p->d_ops);
     dev_free(p, p->d_runs);
     dev_free(p, p->d_rimg);
-    jit_release(p->jit_lib);
-    p->jit_lib = nullptr;
+    jit_release(p->jit_libs);
+    p->jit_libs.clear();
     dev_free(p, p->d_regops);
     dev_free(p, p->d_rounds);
     dev_free(p, p->d_status);

@@ -197,9 +197,10 @@ bool build_register_rounds(const std::vector<TileOp<float2>> &ops, int op_begin,
 // Specialised register passes (jit.cu): generate, compile (NVRTC) and load one
 // kernel per pass; QSIM_EUNSUPPORTED (with *log) when NVRTC is unavailable.
 int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
-              const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs, cudaLibrary_t *lib,
-              std::vector<cudaKernel_t> *kernels, std::string *log);
+              const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs,
+              std::vector<cudaLibrary_t> *libs, std::vector<cudaKernel_t> *kernels, std::string *log);
 void jit_release(cudaLibrary_t lib);
+void jit_release(const std::vector<cudaLibrary_t> &libs);
 // The persistent trajectory kernel in register rounds ("qs_traj"): passes with
 // their rounds, op j of pass p = regops[passes[p].op_begin + j] whose gate is
 // trajectory op src[p][j]; __launch_bounds__(256, min_blocks).
