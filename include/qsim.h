@@ -75,7 +75,9 @@ typedef struct qsim_gate {
 /* How a circuit is executed.  Every mode computes the same gates in the same
  * order; they differ in how many gates one pass over the state vector applies. */
 typedef enum {
-    QSIM_MODE_AUTO = 0,     /* the autotuned choice for (M, precision) */
+    QSIM_MODE_AUTO = 0,     /* complex64 with M >= 20: the tile passes or the fused blocks, whichever a
+                             * time model of the planned passes predicts faster (qsim_plan_describe
+                             * prints the estimates); otherwise the tile passes */
     QSIM_MODE_UNFUSED = 1,  /* one kernel launch per gate */
     QSIM_MODE_TILED = 2,    /* shared-memory tiles: many gates per pass over the vector */
     QSIM_MODE_FUSED = 3     /* runs of gates merged into dense 2^k x 2^k blocks (tensor cores) */

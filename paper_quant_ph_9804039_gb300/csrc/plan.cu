@@ -60,6 +60,7 @@ struct qsim_plan {
     std::vector<cudaLibrary_t> jit_libs;
     std::vector<cudaKernel_t> jit_k;
     std::string jit_log;
+    std::string auto_log;  // the AUTO mode's estimates
     int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
     int fuse_k = 0;
     // non-null: device tables are allocated and freed stream-ordered on this
@@ -1095,6 +1096,75 @@ void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
     }
 }
 
+// ------------------------------------------------------------ AUTO mode
+// A rough time model for choosing between the tile passes and the fused
+// tensor-core blocks (complex64): a pass or a block moves 16 * 2^M bytes; a
+// register pass also spends the arithmetic of its ops, at a sustained FP32
+// rate; a fused block runs at a fixed fraction of the memory bandwidth.  The
+// constants are this simulator's measurements on GB300 (tile passes at copy
+// speed ~6.0 TB/s, fused blocks ~5.0 TB/s, register-pass arithmetic at ~2.2e13
+// FMA/s, permutation passes ~3.6 TB/s).
+constexpr double kModelPassBw = 6.0e12, kModelFusedBw = 5.0e12, kModelPermBw = 3.6e12, kModelFma = 2.2e13;
+
+int count_fused_blocks(const std::vector<Gate> &gates, int k) {
+    std::vector<int> rem(gates.size());
+    for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
+    int blocks = 0;
+    while (!rem.empty()) {
+        uint64_t defN = 0, defA = 0, Q = 0;
+        std::vector<int> keep;
+        for (int gi : rem) {
+            const Gate &g = gates[size_t(gi)];
+            const uint64_t N = g.nondiag() ? bit(g.t) : 0;
+            const uint64_t A = bit(g.t) | g.cmask;
+            if (!((N & defA) || (A & defN)) && __builtin_popcountll(Q | A) <= k) {
+                Q |= A;
+            } else {
+                keep.push_back(gi);
+                defN |= N;
+                defA |= A;
+            }
+        }
+        ++blocks;
+        rem.swap(keep);
+    }
+    return blocks;
+}
+
+// FMA-equivalent operations per amplitude of one register op.
+double regop_cost(const RegOp &op, int S) {
+    const double touched = double(__builtin_popcount(op.smask)) / double(S) / double(1u << __builtin_popcount(op.nmask));
+    const int c = op.code;
+    if (c >= RC_HAD) return 2.0;
+    if (c < RC_RDENSE) return 16.0 * touched * 2.0;  // pair kinds: smask counts pairs
+    if (c < RC_SWAP) return 8.0 * touched * 2.0;
+    if (c < RC_PHASE_ALL) return 0.5;
+    if (c == RC_TAB) return 10.0 * touched;
+    if (c == RC_PHRUN) return 24.0;
+    return 8.0 * touched;
+}
+
+double model_seconds(const qsim_plan *p, const std::vector<RegOp> &regops) {
+    const double N = std::ldexp(1.0, p->M);
+    double t = 0;
+    for (const Step &st : p->steps) {
+        if (st.type == S_PERM) {
+            t += 16.0 * N / kModelPermBw;
+        } else if (st.type == S_TILE) {
+            double fma = 0;
+            const int S = 1 << std::max(0, st.d.b - kRegThreadBits);
+            if (st.d.round_count > 0)
+                for (int j = 0; j < st.d.op_count; ++j) fma += regop_cost(regops[size_t(st.d.op_begin + j)], S);
+            else
+                fma = 16.0 * double(st.d.op_count);
+            t += std::max(16.0 * N / kModelPassBw, fma * N / kModelFma);
+        } else if (st.type == S_FUSED) {
+            t += 16.0 * N / kModelFusedBw;
+        }
+    }
+    return t;
+}
+
 int dev_alloc(const qsim_plan *p, void **dev, size_t bytes) {
     if (p->alloc_stream) QS_CUDA(cudaMallocAsync(dev, bytes, p->alloc_stream));
     else QS_CUDA(cudaMalloc(dev, bytes));
@@ -1207,6 +1277,35 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
         return QSIM_EINVAL;
     }
     int mode = o.mode == QSIM_MODE_AUTO ? QSIM_MODE_TILED : o.mode;
+    if (o.mode == QSIM_MODE_AUTO && prec == QSIM_C64 && M >= 20) {
+        // plan the tile passes on a scratch plan (host only), estimate both forms
+        qsim_plan scratch;
+        scratch.M = M;
+        scratch.prec = prec;
+        scratch.gates = p->gates;
+        split_row_phases(scratch.gates);
+        const int b = std::min(o.tile_bits ? o.tile_bits : default_tile_bits(prec), M);
+        std::vector<TileOp<float2>> ops;
+        std::vector<unsigned char> runs;
+        std::vector<int> all(scratch.gates.size());
+        for (size_t i = 0; i < all.size(); ++i) all[i] = int(i);
+        plan_tiled(&scratch, b, all, ops, runs);
+        std::vector<RegOp> regops;
+        std::vector<RoundDesc> rounds;
+        for (Step &st : scratch.steps) {
+            if (st.type != S_TILE) continue;
+            const int RB = st.d.b - kRegThreadBits;
+            if (RB < 3 || RB > 4) continue;
+            TilePassDesc d = st.d;
+            if (build_rounds(ops, st.d.op_begin, st.d.op_count, d, RB, regops, rounds, runs)) st.d = d;
+        }
+        const double t_tiled = model_seconds(&scratch, regops);
+        const double t_fused = double(count_fused_blocks(p->gates, 5)) * 16.0 * std::ldexp(1.0, M) / kModelFusedBw;
+        if (t_fused < t_tiled) mode = QSIM_MODE_FUSED;
+        char line[160];
+        std::snprintf(line, sizeof line, "auto: tiled %.3g s, fused %.3g s (model)", t_tiled, t_fused);
+        p->auto_log = line;
+    }
     // The tensor-core kernel runs 4- or 5-qubit blocks of complex64 states
     // with at least 2^(k+7) amplitudes; anything else takes the tile passes.
     const int k_eff = o.fuse_k == 0 ? 5 : std::max(3, o.fuse_k);
@@ -1451,6 +1550,7 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
     static const char *kinds[] = {"DENSE", "RDENSE", "SWAP"};
     add("M=%d prec=%s mode=%d steps=%zu\n", p->M, p->prec == QSIM_C64 ? "c64" : "c128", p->mode, p->steps.size());
     if (!p->jit_log.empty()) add("specialisation: %s\n", p->jit_log.c_str());
+    if (!p->auto_log.empty()) add("%s\n", p->auto_log.c_str());
     for (size_t j = 0; j < p->steps.size(); ++j) {
         const Step &st = p->steps[j];
         if (st.type == S_GATE) {

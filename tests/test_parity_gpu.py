@@ -473,3 +473,19 @@ def test_specialised_passes(orc, kind, M, tile_bits):
     spec.execute(b)
     assert np.array_equal(a.get(), b.get())
     _close(b.get(), orc.run(M, recs, x128, nthreads=NT), "c64")
+
+
+def test_auto_mode_picks_by_time_model(orc):
+    """AUTO keeps the tile passes for a phase-heavy circuit (the QFT) and takes
+    the fused tensor-core blocks for a dense-heavy one (Haar brickwork); both
+    results agree with the oracle."""
+    M = 20
+    x, x128 = _input(M, "c64")
+    for recs, want in ((W.circuit_c2_qft(M, sigma=1e-4)["noisy"], qs.MODE_TILED),
+                       (W.circuit_c4_brickwork_toffoli(M, layers=24)["noisy"], qs.MODE_FUSED)):
+        plan = qs.Plan(M, recs, mode="auto")
+        assert "auto: tiled" in plan.describe()
+        assert plan.stats()["mode"] == want, plan.describe().splitlines()[:3]
+        st = qs.State(M).set(x)
+        plan.execute(st)
+        _close(st.get(), orc.run(M, recs, x128, nthreads=NT), "c64")
