@@ -48,7 +48,7 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="qft-m28-c64", choices=sorted(WORKLOADS))
@@ -123,14 +123,21 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.lines = []
+        self.start = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once nvidia-smi is sampling: earlier lines
+            # are not counted
+            t0 = time.time()
+            while not self.lines and self.proc.poll() is None and time.time() - t0 < 5.0:
+                time.sleep(0.01)
+            self.start = len(self.lines)
         except OSError:
             self.proc = None
         return self
@@ -151,7 +158,7 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.start:] or self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -566,8 +573,10 @@ def run_brickwork(args, rank, world, local):
     noisy = qs.State(M, device=dev, stream=stream)
     peak, peak_src = measured_peaks()
     modes = {}
-    for mode, steps, warm in (("tiled", max(1, args.steps), max(1, min(args.warmup, 2))),
-                              ("fused", max(1, args.steps), max(1, min(args.warmup, 2))),
+    # a step here takes seconds: at most 5 timed steps per mode
+    k = max(1, min(args.steps, 5))
+    for mode, steps, warm in (("tiled", k, max(1, min(args.warmup, 2))),
+                              ("fused", k, max(1, min(args.warmup, 2))),
                               ("unfused", 1, 0)):
         if mode == "unfused" and args.no_unfused:
             continue
