@@ -213,27 +213,70 @@ void emit_op(Src &out, const RegOp &op, const RoundDesc &rd, int RB, const TileP
     out("   }\n  }\n");
 }
 
+// Thread tid's base index in a round: tid with a zero inserted at each slot position.
+uint32_t round_base(const RoundDesc &rd, int RB, uint32_t tid) {
+    uint32_t i0 = tid;
+    for (int k = 0; k < RB; ++k) {
+        const int q = rd.pos[k];
+        i0 = ((i0 >> q) << (q + 1)) | (i0 & ((1u << q) - 1));
+    }
+    return i0;
+}
+
+// Layout of a staged tile in shared memory.  The tile arrives as 16-byte
+// chunks (amplitudes 2j, 2j + 1); chunk j sits at chunk position
+// j ^ ((j >> sh) & mask).  With sh >= 3 the 8 consecutive chunks that a
+// quarter-warp copies stay on distinct banks; sh and mask are chosen per pass
+// for the first round's reads (16-byte reads of both slots' amplitudes when a
+// slot is on tile position 0).  The map is linear: pos(x ^ y) = pos(x) ^ pos(y).
+struct Stage {
+    int sh = 3;
+    uint32_t mask = 0;
+    uint32_t pos(uint32_t x) const { return x ^ (((x >> (sh + 1)) & mask) << 1); }
+};
+
+Stage choose_stage(const TilePassDesc &d, const RoundDesc &rd, int RB) {
+    const int S = 1 << RB;
+    const bool pair = rd.pos[0] == 0;
+    auto cost = [&](const Stage &g) {
+        long c = 0;
+        uint32_t addr[32];
+        for (uint32_t w = 0; w < 8; ++w)
+            for (int r = 0; r < S; r += pair ? 2 : 1) {
+                for (uint32_t l = 0; l < 32; ++l) addr[l] = 8u * g.pos(round_base(rd, RB, 32 * w + l) | dep_of(rd, RB, r));
+                c += smem_wavefronts(addr, pair ? 16 : 8);
+            }
+        return c;
+    };
+    Stage best;
+    long best_cost = cost(best);
+    for (int sh = 3; sh <= d.b - 2; ++sh)
+        for (uint32_t mask : {7u, 15u, 31u}) {
+            Stage g;
+            g.sh = sh;
+            g.mask = mask;
+            const long c = cost(g);
+            if (c < best_cost) {
+                best_cost = c;
+                best = g;
+            }
+        }
+    return best;
+}
+
+// One pass as a kernel.  Each block walks its tiles with the next tile's
+// amplitudes in flight (cp.async into the second of two shared-memory
+// buffers) while the current one goes through the register rounds; the first
+// round reads the staged tile, later rounds exchange through the same buffer,
+// and the last round stores straight to device memory.  A leading op-free
+// round (kept by the general kernel to read device memory coalesced) is
+// skipped: the staged copy is coalesced whatever the first round's slots.
 std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &regops,
                       const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs) {
     const int RB = d.b - kRegThreadBits, S = 1 << RB;
     Src out;
     int tq[32];
     for (int t = 0; t < d.b; ++t) tq[t] = t < d.L ? t : d.hpos[t - d.L];
-    out("__constant__ int kTq_%d[%d] = {", idx, d.b);
-    for (int t = 0; t < d.b; ++t) out("%d%s", tq[t], t + 1 < d.b ? ", " : "};\n");
-    out("__constant__ int kOpos_%d[%d] = {", idx, d.nout > 0 ? d.nout : 1);
-    if (d.nout == 0) out("0};\n");
-    for (int k = 0; k < d.nout; ++k) out("%d%s", d.opos[k], k + 1 < d.nout ? ", " : "};\n");
-    out("extern \"C\" __global__ void __launch_bounds__(256, 3)\n");
-    out("qs_pass_%d(float2 *dst, const float2 *src, const unsigned char *__restrict__ runs, qs_u64 ntiles) {\n", idx);
-    out("  const int *kTq = kTq_%d; const int *kOpos = kOpos_%d; (void)kTq; (void)kOpos;\n", idx, idx);
-    if (d.round_count > 1) out("  __shared__ float2 s[%d];\n", 1 << d.b);
-    out("  __shared__ qs_u32 ps_cl[2][16], ps_ktw[2][8];\n  int nrun = 0; (void)nrun;\n");
-    out("  const qs_u32 tid = threadIdx.x;\n  float2 v[%d];\n", S);
-    out("  for (qs_u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {\n");
-    out("   qs_u64 base = 0");
-    for (int k = 0; k < d.nout; ++k) out(" | (((tile >> %d) & 1ull) << %d)", k, d.opos[k]);
-    out(";\n");
     const uint32_t lowmask = (1u << d.L) - 1;
     auto goff_const = [&](uint32_t i) {  // device offset of tile-local index i
         uint64_t o = i & lowmask;
@@ -242,29 +285,90 @@ std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &
         return o;
     };
     auto swz = [](uint32_t x) { return x ^ ((x >> 4) & 15u); };
-    for (int r = 0; r < d.round_count; ++r) {
+    const int r0 = d.round_count > 1 && rounds[size_t(d.round_begin)].op_count == 0 ? 1 : 0;
+    const RoundDesc &rd0 = rounds[size_t(d.round_begin + r0)];
+    const Stage stg = choose_stage(d, rd0, RB);
+    const bool pair0 = rd0.pos[0] == 0;
+    const int nchunk = 1 << (d.b - 1 - kRegThreadBits);  // 16-byte chunks per thread and tile
+
+    out("__constant__ int kTq_%d[%d] = {", idx, d.b);
+    for (int t = 0; t < d.b; ++t) out("%d%s", tq[t], t + 1 < d.b ? ", " : "};\n");
+    out("__constant__ int kOpos_%d[%d] = {", idx, d.nout > 0 ? d.nout : 1);
+    if (d.nout == 0) out("0};\n");
+    for (int k = 0; k < d.nout; ++k) out("%d%s", d.opos[k], k + 1 < d.nout ? ", " : "};\n");
+    out("extern \"C\" __global__ void __launch_bounds__(256, 3)\n");
+    out("qs_pass_%d(float2 *dst, const float2 *src, const unsigned char *__restrict__ runs, qs_u64 ntiles) {\n", idx);
+    out("  const int *kTq = kTq_%d; const int *kOpos = kOpos_%d; (void)kTq; (void)kOpos;\n", idx, idx);
+    out("  extern __shared__ __align__(16) float2 qs_sm[];\n");
+    out("  __shared__ qs_u32 ps_cl[2][16], ps_ktw[2][8];\n  int nrun = 0; (void)nrun;\n");
+    out("  const qs_u32 tid = threadIdx.x;\n  float2 v[%d];\n", S);
+    // device offset of tile-local index 2 tid (the thread's first chunk)
+    out("  const qs_u64 ld_off = (qs_u64)((tid << 1) & %uu)", lowmask);
+    for (int t = std::max(1, d.L); t <= kRegThreadBits; ++t)
+        out(" | ((qs_u64)((tid >> %d) & 1u) << %d)", t - 1, d.hpos[t - d.L]);
+    out(";\n");
+    auto emit_base = [&](const char *name, const char *tile) {
+        out("   const qs_u64 %s = 0", name);
+        for (int k = 0; k < d.nout; ++k) out(" | (((%s >> %d) & 1ull) << %d)", tile, k, d.opos[k]);
+        out(";\n");
+    };
+    auto emit_issue = [&](const char *tile, const char *buf) {
+        out("   {\n");
+        emit_base("nb", tile);
+        out("   const float2 *g = src + (nb | ld_off);\n");
+        out("   const qs_u32 sa = (qs_u32)__cvta_generic_to_shared(%s);\n", buf);
+        for (int k = 0; k < nchunk; ++k) {
+            out("   { const qs_u32 j = tid + %uu; asm volatile(\"cp.async.cg.shared.global [%%0], [%%1], 16;\" :: "
+                "\"r\"(sa + ((j ^ ((j >> %d) & %uu)) << 4)), \"l\"(g + %lluull) : \"memory\"); }\n",
+                unsigned(k << kRegThreadBits), stg.sh, stg.mask,
+                (unsigned long long)goff_const(uint32_t(k) << (kRegThreadBits + 1)));
+        }
+        out("   asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n   }\n");
+    };
+    out("  float2 *const sb0 = qs_sm, *const sb1 = qs_sm + %u;\n", 1u << d.b);
+    out("  if (blockIdx.x < ntiles) {\n   const qs_u64 t0 = blockIdx.x;\n");
+    emit_issue("t0", "sb0");
+    out("  }\n  qs_u32 it = 0;\n");
+    out("  for (qs_u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {\n");
+    out("   float2 *const s = (it & 1u) ? sb1 : sb0;\n");
+    out("   asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");\n   __syncthreads();\n");
+    out("   if (tile + gridDim.x < ntiles) {\n   float2 *const nbuf = (it & 1u) ? sb0 : sb1;\n");
+    out("   const qs_u64 nt = tile + gridDim.x;\n");
+    emit_issue("nt", "nbuf");
+    out("   }\n");
+    emit_base("base", "tile");
+    for (int r = r0; r < d.round_count; ++r) {
         const RoundDesc &rd = rounds[size_t(d.round_begin + r)];
+        const bool last = r + 1 == d.round_count;
         out("   {  // round %d\n", r);
         out("   qs_u32 i0 = tid;\n");
         for (int k = 0; k < RB; ++k) {
             const int q = rd.pos[k];
             out("   i0 = ((i0 >> %d) << %d) | (i0 & %uu);\n", q, q + 1, (1u << q) - 1);
         }
-        if (r == 0 || r + 1 == d.round_count) {
+        if (last) {
             out("   const qs_u64 gi0 = (qs_u64)(i0 & %uu)", lowmask);
             for (int h = 0; h < d.nh; ++h) out(" | ((qs_u64)((i0 >> %d) & 1u) << %d)", d.L + h, d.hpos[h]);
             out(";\n");
         }
-        if (d.round_count > 1) out("   const qs_u32 si0 = i0 ^ ((i0 >> 4) & 15u);\n");
-        if (r == 0) {
-            for (int c = 0; c < S; ++c)
-                out("   v[%d] = src[base | gi0 | %lluull];\n", c, (unsigned long long)goff_const(dep_of(rd, RB, c)));
+        if (r > r0 || !last) out("   const qs_u32 si0 = i0 ^ ((i0 >> 4) & 15u);\n");
+        if (r == r0) {
+            out("   const qs_u32 p0 = i0 ^ (((i0 >> %d) & %uu) << 1);\n", stg.sh + 1, stg.mask);
+            if (pair0) {
+                out("   const float4 *s4 = reinterpret_cast<const float4 *>(s);\n");
+                for (int c = 0; c < S; c += 2)
+                    out("   { const float4 t = s4[(p0 ^ %uu) >> 1]; v[%d] = make_float2(t.x, t.y); "
+                        "v[%d] = make_float2(t.z, t.w); }\n",
+                        stg.pos(dep_of(rd, RB, c)), c, c + 1);
+            } else {
+                for (int c = 0; c < S; ++c) out("   v[%d] = s[p0 ^ %uu];\n", c, stg.pos(dep_of(rd, RB, c)));
+            }
         } else {
             for (int c = 0; c < S; ++c) out("   v[%d] = s[si0 ^ %uu];\n", c, swz(dep_of(rd, RB, c)));
         }
         for (int k = 0; k < rd.op_count; ++k)
             emit_op(out, regops[size_t(d.op_begin + rd.op_begin + k)], rd, RB, d, runs);
-        if (r + 1 == d.round_count) {
+        if (last) {
             if (d.pscale_on)
                 for (int c = 0; c < S; ++c)
                     out("   v[%d] = make_float2(fmaf(v[%d].x, %s, v[%d].x * %s), fmaf(v[%d].y, %s, v[%d].y * %s));\n", c,
@@ -454,6 +558,11 @@ int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector
     for (size_t i = 0; i < np; ++i) {
         cudaError_t e = cudaLibraryLoadData(&(*libs)[i], cubins[i].data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
         if (e == cudaSuccess) e = cudaLibraryGetKernel(&(*kernels)[i], (*libs)[i], "qs_pass_0");
+        int dev = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)  // two staged tiles
+            e = cudaKernelSetAttributeForDevice((*kernels)[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                int(jit_pass_smem_bytes(*passes[i])), dev);
         if (e != cudaSuccess) {
             jit_release(*libs);
             libs->clear();
@@ -488,6 +597,8 @@ int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::ve
     return QSIM_OK;
 }
 
+size_t jit_pass_smem_bytes(const TilePassDesc &d) { return size_t(2) * sizeof(float2) << d.b; }
+
 void jit_release(cudaLibrary_t lib) {
     if (lib) cudaLibraryUnload(lib);
 }
@@ -505,7 +616,8 @@ int launch_jit_pass(cudaKernel_t k, void *dst, const void *src, int M, const Til
     const void *sp = src;
     const void *rp = runs_dev;
     void *args[] = {&dp, &sp, &rp, &ntiles};
-    QS_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(k), dim3(unsigned(grid)), dim3(256), args, 0, s));
+    QS_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(k), dim3(unsigned(grid)), dim3(256), args,
+                             jit_pass_smem_bytes(d), s));
     return QSIM_OK;
 }
 

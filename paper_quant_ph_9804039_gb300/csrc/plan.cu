@@ -1238,6 +1238,8 @@ bool build_register_rounds(const std::vector<TileOp<float2>> &ops, int op_begin,
     return build_rounds(ops, op_begin, op_count, d, RB, regops, rounds, runs);
 }
 
+int smem_wavefronts(const uint32_t *addr, int width) { return wavefronts(addr, width); }
+
 }  // namespace qs
 
 namespace qs {

@@ -207,6 +207,7 @@ void jit_release(const std::vector<cudaLibrary_t> &libs);
 int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::vector<RegOp> &regops,
                    const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks,
                    cudaLibrary_t *lib, cudaKernel_t *kernel, std::string *log);
+size_t jit_pass_smem_bytes(const TilePassDesc &d);  // the two staged tiles of a specialised pass
 int launch_jit_pass(cudaKernel_t k, void *dst, const void *src, int M, const TilePassDesc &d, const void *runs_dev,
                     cudaStream_t s);
 constexpr int kTileOpSmemBytes = 24 * 1024;  // a pass's ops are staged in shared memory up to this size
@@ -254,6 +255,9 @@ struct PermDesc {
     int opos[QSIM_MAX_QUBITS], opi[QSIM_MAX_QUBITS];
 };
 size_t perm_smem_bytes(const PermDesc &d, qsim_prec prec);  // at most 96 KiB
+// Shared-memory wavefronts of one warp access: lane byte addresses, `width`
+// (4, 8 or 16) bytes per lane.
+int smem_wavefronts(const uint32_t *addr, int width);
 int launch_perm(void *dst, const void *src, int M, qsim_prec prec, const PermDesc &d, cudaStream_t s);
 
 // -------------------------------------------------------------- reductions
