@@ -21,6 +21,7 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <mutex>
 #include <thread>
 #include <string>
@@ -223,22 +224,46 @@ uint32_t round_base(const RoundDesc &rd, int RB, uint32_t tid) {
     return i0;
 }
 
-// Layout of a staged tile in shared memory.  The tile arrives as 16-byte
-// chunks (amplitudes 2j, 2j + 1); chunk j sits at chunk position
-// j ^ ((j >> sh) & mask).  With sh >= 3 the 8 consecutive chunks that a
-// quarter-warp copies stay on distinct banks; sh and mask are chosen per pass
-// for the first round's reads (16-byte reads of both slots' amplitudes when a
-// slot is on tile position 0).  The map is linear: pos(x ^ y) = pos(x) ^ pos(y).
+// Layout of a staged tile in shared memory: the index XOR up to two shifted
+// copies of its higher bits, so a linear map (pos(x ^ y) = pos(x) ^ pos(y))
+// and a bijection (each term moves bits to lower positions only).
+// keep0: the tile arrives as 16-byte chunks (amplitudes 2j, 2j + 1) and the
+// terms act on the chunk index j; with shifts >= 3 the 8 consecutive chunks
+// that a quarter-warp copies stay on distinct banks.  Otherwise (8-byte
+// copies, the gathering first pass) they act on the amplitude index.  Shifts
+// and masks are chosen per pass with the bank model over the first round's
+// reads (16-byte reads of both slots' amplitudes when a slot is on tile
+// position 0 and pairs stay adjacent) and, for 8-byte copies, the writes.
 struct Stage {
-    int sh = 3;
-    uint32_t mask = 0;
-    uint32_t pos(uint32_t x) const { return x ^ (((x >> (sh + 1)) & mask) << 1); }
+    int sh[2] = {3, 3};
+    uint32_t mask[2] = {0, 0};
+    bool keep0 = true;
+    uint32_t pos(uint32_t x) const {
+        const int k = keep0 ? 1 : 0;
+        uint32_t f = 0;
+        for (int t = 0; t < 2; ++t) f ^= ((x >> (sh[t] + k)) & mask[t]) << k;
+        return x ^ f;
+    }
 };
 
-Stage choose_stage(const TilePassDesc &d, const RoundDesc &rd, int RB) {
+// A gathering first pass: element u of the source-order enumeration of a
+// tile (u's bit k <-> source bit sbit[k]) is tile-local index scatter(u)
+// (u's bit k <-> tile position lam[k]).
+struct Gather {
+    int lam[32];
+    int sbit[32];
+    uint32_t scatter(uint32_t u, int b) const {
+        uint32_t x = 0;
+        for (int k = 0; k < b; ++k)
+            if ((u >> k) & 1) x |= 1u << lam[k];
+        return x;
+    }
+};
+
+Stage choose_stage(const TilePassDesc &d, const RoundDesc &rd, int RB, const Gather *ga) {
     const int S = 1 << RB;
-    const bool pair = rd.pos[0] == 0;
     auto cost = [&](const Stage &g) {
+        const bool pair = rd.pos[0] == 0 && g.keep0;
         long c = 0;
         uint32_t addr[32];
         for (uint32_t w = 0; w < 8; ++w)
@@ -246,20 +271,47 @@ Stage choose_stage(const TilePassDesc &d, const RoundDesc &rd, int RB) {
                 for (uint32_t l = 0; l < 32; ++l) addr[l] = 8u * g.pos(round_base(rd, RB, 32 * w + l) | dep_of(rd, RB, r));
                 c += smem_wavefronts(addr, pair ? 16 : 8);
             }
+        if (ga)  // the copies' writes, 8 bytes per lane
+            for (uint32_t u0 = 0; u0 < (1u << d.b); u0 += 32) {
+                for (uint32_t l = 0; l < 32; ++l) addr[l] = 8u * g.pos(ga->scatter(u0 + l, d.b));
+                c += smem_wavefronts(addr, 8);
+            }
         return c;
     };
     Stage best;
+    best.keep0 = ga == nullptr;
     long best_cost = cost(best);
-    for (int sh = 3; sh <= d.b - 2; ++sh)
-        for (uint32_t mask : {7u, 15u, 31u}) {
-            Stage g;
-            g.sh = sh;
-            g.mask = mask;
-            const long c = cost(g);
-            if (c < best_cost) {
-                best_cost = c;
-                best = g;
+    const uint32_t masks[] = {7u, 15u, 31u};
+    auto consider = [&](const Stage &g) {
+        const long c = cost(g);
+        if (c < best_cost) {
+            best_cost = c;
+            best = g;
+        }
+    };
+    if (!ga) {  // 16-byte chunks: one term
+        for (int sh = 3; sh <= d.b - 2; ++sh)
+            for (uint32_t m : masks) {
+                Stage g;
+                g.sh[0] = sh;
+                g.mask[0] = m;
+                consider(g);
             }
+        return best;
+    }
+    for (int sh = 1; sh <= d.b - 1; ++sh)  // 8-byte copies: one or two terms
+        for (uint32_t m : masks) {
+            Stage g;
+            g.keep0 = false;
+            g.sh[0] = sh;
+            g.mask[0] = m;
+            consider(g);
+            for (int sh2 = sh + 1; sh2 <= d.b - 1; ++sh2)
+                for (uint32_t m2 : masks) {
+                    g.sh[1] = sh2;
+                    g.mask[1] = m2;
+                    consider(g);
+                }
         }
     return best;
 }
@@ -271,8 +323,16 @@ Stage choose_stage(const TilePassDesc &d, const RoundDesc &rd, int RB) {
 // and the last round stores straight to device memory.  A leading op-free
 // round (kept by the general kernel to read device memory coalesced) is
 // skipped: the staged copy is coalesced whatever the first round's slots.
+//
+// With `gather` (a qubit permutation, an involution) the pass also applies
+// that permutation to its input on the way in: the amplitude of physical
+// index y is read from source index x, bit gather[q] of x = bit q of y.  Its
+// tile holds the qubits whose source bits are 0..3 or more, so each warp
+// still reads whole runs of the source; the copies are 8 bytes each, in
+// source order, into the shared-memory layout chosen for them.
 std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &regops,
-                      const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs) {
+                      const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs,
+                      const std::vector<int> *gather = nullptr) {
     const int RB = d.b - kRegThreadBits, S = 1 << RB;
     Src out;
     int tq[32];
@@ -287,9 +347,26 @@ std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &
     auto swz = [](uint32_t x) { return x ^ ((x >> 4) & 15u); };
     const int r0 = d.round_count > 1 && rounds[size_t(d.round_begin)].op_count == 0 ? 1 : 0;
     const RoundDesc &rd0 = rounds[size_t(d.round_begin + r0)];
-    const Stage stg = choose_stage(d, rd0, RB);
-    const bool pair0 = rd0.pos[0] == 0;
+    Gather ga{};
+    if (gather) {  // tile positions in the order of their source bits
+        int order[32];
+        for (int t = 0; t < d.b; ++t) order[t] = t;
+        std::sort(order, order + d.b, [&](int a, int c) { return (*gather)[tq[a]] < (*gather)[tq[c]]; });
+        for (int k = 0; k < d.b; ++k) {
+            ga.lam[k] = order[k];
+            ga.sbit[k] = (*gather)[tq[order[k]]];
+        }
+    }
+    const Stage stg = choose_stage(d, rd0, RB, gather ? &ga : nullptr);
+    const bool pair0 = rd0.pos[0] == 0 && stg.keep0;
     const int nchunk = 1 << (d.b - 1 - kRegThreadBits);  // 16-byte chunks per thread and tile
+    auto emit_pos = [&](const char *name, const char *x) {  // name = stg.pos(x)
+        const int k = stg.keep0 ? 1 : 0;
+        out("  const qs_u32 %s = %s", name, x);
+        for (int t = 0; t < 2; ++t)
+            if (stg.mask[t]) out(" ^ (((%s >> %d) & %uu) << %d)", x, stg.sh[t] + k, stg.mask[t], k);
+        out(";\n");
+    };
 
     out("__constant__ int kTq_%d[%d] = {", idx, d.b);
     for (int t = 0; t < d.b; ++t) out("%d%s", tq[t], t + 1 < d.b ? ", " : "};\n");
@@ -302,29 +379,59 @@ std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &
     out("  extern __shared__ __align__(16) float2 qs_sm[];\n");
     out("  __shared__ qs_u32 ps_cl[2][16], ps_ktw[2][8];\n  int nrun = 0; (void)nrun;\n");
     out("  const qs_u32 tid = threadIdx.x;\n  float2 v[%d];\n", S);
-    // device offset of tile-local index 2 tid (the thread's first chunk)
-    out("  const qs_u64 ld_off = (qs_u64)((tid << 1) & %uu)", lowmask);
-    for (int t = std::max(1, d.L); t <= kRegThreadBits; ++t)
-        out(" | ((qs_u64)((tid >> %d) & 1u) << %d)", t - 1, d.hpos[t - d.L]);
-    out(";\n");
-    auto emit_base = [&](const char *name, const char *tile) {
+    auto emit_base = [&](const char *name, const char *tile, bool src_bits) {
         out("   const qs_u64 %s = 0", name);
-        for (int k = 0; k < d.nout; ++k) out(" | (((%s >> %d) & 1ull) << %d)", tile, k, d.opos[k]);
+        for (int k = 0; k < d.nout; ++k)
+            out(" | (((%s >> %d) & 1ull) << %d)", tile, k, src_bits ? (*gather)[d.opos[k]] : d.opos[k]);
         out(";\n");
     };
-    auto emit_issue = [&](const char *tile, const char *buf) {
-        out("   {\n");
-        emit_base("nb", tile);
-        out("   const float2 *g = src + (nb | ld_off);\n");
-        out("   const qs_u32 sa = (qs_u32)__cvta_generic_to_shared(%s);\n", buf);
-        for (int k = 0; k < nchunk; ++k) {
-            out("   { const qs_u32 j = tid + %uu; asm volatile(\"cp.async.cg.shared.global [%%0], [%%1], 16;\" :: "
-                "\"r\"(sa + ((j ^ ((j >> %d) & %uu)) << 4)), \"l\"(g + %lluull) : \"memory\"); }\n",
-                unsigned(k << kRegThreadBits), stg.sh, stg.mask,
-                (unsigned long long)goff_const(uint32_t(k) << (kRegThreadBits + 1)));
-        }
-        out("   asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n   }\n");
-    };
+    std::function<void(const char *, const char *)> emit_issue;
+    if (!gather) {
+        // device offset of tile-local index 2 tid (the thread's first chunk)
+        out("  const qs_u64 ld_off = (qs_u64)((tid << 1) & %uu)", lowmask);
+        for (int t = std::max(1, d.L); t <= kRegThreadBits; ++t)
+            out(" | ((qs_u64)((tid >> %d) & 1u) << %d)", t - 1, d.hpos[t - d.L]);
+        out(";\n");
+        emit_issue = [&](const char *tile, const char *buf) {
+            out("   {\n");
+            emit_base("nb", tile, false);
+            out("   const float2 *g = src + (nb | ld_off);\n");
+            out("   const qs_u32 sa = (qs_u32)__cvta_generic_to_shared(%s);\n", buf);
+            for (int k = 0; k < nchunk; ++k) {
+                out("   { const qs_u32 j = tid + %uu; asm volatile(\"cp.async.cg.shared.global [%%0], [%%1], 16;\" :: "
+                    "\"r\"(sa + ((j ^ ((j >> %d) & %uu)) << 4)), \"l\"(g + %lluull) : \"memory\"); }\n",
+                    unsigned(k << kRegThreadBits), stg.sh[0], stg.mask[0],
+                    (unsigned long long)goff_const(uint32_t(k) << (kRegThreadBits + 1)));
+            }
+            out("   asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n   }\n");
+        };
+    } else {
+        // element u = tid + 256 k of the source-order enumeration: its source
+        // offset within the tile and (laid out) shared-memory position
+        out("  const qs_u32 lx = 0u");
+        for (int k = 0; k < kRegThreadBits; ++k) out(" | (((tid >> %d) & 1u) << %d)", k, ga.lam[k]);
+        out(";\n");
+        out("  const qs_u64 ld_off = 0ull");
+        for (int k = 0; k < kRegThreadBits; ++k) out(" | ((qs_u64)((tid >> %d) & 1u) << %d)", k, ga.sbit[k]);
+        out(";\n");
+        emit_pos("plx", "lx");
+        emit_issue = [&](const char *tile, const char *buf) {
+            out("   {\n");
+            emit_base("nb", tile, true);
+            out("   const float2 *g = src + (nb | ld_off);\n");
+            out("   const qs_u32 sa = (qs_u32)__cvta_generic_to_shared(%s);\n", buf);
+            for (uint32_t k = 0; k < (1u << (d.b - kRegThreadBits)); ++k) {
+                uint64_t so = 0;
+                for (int j = 0; j < d.b - kRegThreadBits; ++j)
+                    if ((k >> j) & 1) so |= uint64_t(1) << ga.sbit[kRegThreadBits + j];
+                const uint32_t xc = ga.scatter(k << kRegThreadBits, d.b);
+                out("   asm volatile(\"cp.async.ca.shared.global [%%0], [%%1], 8;\" :: \"r\"(sa + ((plx ^ %uu) << 3)), "
+                    "\"l\"(g + %lluull) : \"memory\");\n",
+                    stg.pos(xc), (unsigned long long)so);
+            }
+            out("   asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n   }\n");
+        };
+    }
     out("  float2 *const sb0 = qs_sm, *const sb1 = qs_sm + %u;\n", 1u << d.b);
     out("  if (blockIdx.x < ntiles) {\n   const qs_u64 t0 = blockIdx.x;\n");
     emit_issue("t0", "sb0");
@@ -336,7 +443,7 @@ std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &
     out("   const qs_u64 nt = tile + gridDim.x;\n");
     emit_issue("nt", "nbuf");
     out("   }\n");
-    emit_base("base", "tile");
+    emit_base("base", "tile", false);
     for (int r = r0; r < d.round_count; ++r) {
         const RoundDesc &rd = rounds[size_t(d.round_begin + r)];
         const bool last = r + 1 == d.round_count;
@@ -353,7 +460,7 @@ std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &
         }
         if (r > r0 || !last) out("   const qs_u32 si0 = i0 ^ ((i0 >> 4) & 15u);\n");
         if (r == r0) {
-            out("   const qs_u32 p0 = i0 ^ (((i0 >> %d) & %uu) << 1);\n", stg.sh + 1, stg.mask);
+            emit_pos("p0", "i0");
             if (pair0) {
                 out("   const float4 *s4 = reinterpret_cast<const float4 *>(s);\n");
                 for (int c = 0; c < S; c += 2)
@@ -528,16 +635,17 @@ bool compile_cubin(const std::string &src, const char *name, std::vector<char> *
 // One program per pass, compiled on a pool of host threads (compile time
 // grows faster than linearly with the program, and passes are independent),
 // each loaded as its own library.
-int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
-              const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs,
-              std::vector<cudaLibrary_t> *libs, std::vector<cudaKernel_t> *kernels, std::string *log) {
+int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<const std::vector<int> *> &gathers,
+              const std::vector<RegOp> &regops, const std::vector<RoundDesc> &rounds,
+              const std::vector<unsigned char> &runs, std::vector<cudaLibrary_t> *libs,
+              std::vector<cudaKernel_t> *kernels, std::string *log) {
     if (!nvrtc().ok) {
         if (log) *log = "NVRTC not found";
         return QSIM_EUNSUPPORTED;
     }
     const size_t np = passes.size();
     std::vector<std::string> srcs(np), logs(np);
-    for (size_t i = 0; i < np; ++i) srcs[i] = std::string(kJitHeader) + emit_pass(0, *passes[i], regops, rounds, runs);
+    for (size_t i = 0; i < np; ++i) srcs[i] = std::string(kJitHeader) + emit_pass(0, *passes[i], regops, rounds, runs, i < gathers.size() ? gathers[i] : nullptr);
     std::vector<std::vector<char>> cubins(np);
     std::vector<char> ok(np, 0);
     std::atomic<size_t> next{0};

@@ -59,6 +59,11 @@ struct qsim_plan {
     // specialised register passes (qsim_opts.specialize): one kernel per step, or null
     std::vector<cudaLibrary_t> jit_libs;
     std::vector<cudaKernel_t> jit_k;
+    // swap runs moved to the front (step 0 permutes by front_perm); with
+    // jit_gather_k the first tile pass applies it while reading a separate source
+    std::vector<int> front_perm;
+    cudaKernel_t jit_gather_k = nullptr;
+    mutable bool last_absorbed = false;  // the last execution left the permutation pass to the gather
     std::string jit_log;
     std::string auto_log;  // the AUTO mode's estimates
     int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
@@ -494,7 +499,7 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
                         const int sl = slot_of[op.tpos[j]];
                         if (sl >= 0 && ((c >> sl) & 1)) e |= 1u << j;
                     }
-                    op.cidx[c] = uint8_t(e);
+                    op.cidx[c] = uint16_t(e);
                 }
             }
             {  // dispatch code
@@ -651,6 +656,50 @@ int find_swap_runs(const std::vector<Gate> &g, std::vector<int> &run_of, std::ve
     return nrun;
 }
 
+// Every swap run moved to the front of the circuit.  A run that exchanges
+// qubit positions (pi[q] = new position of q) can be left out if every later
+// gate is relabelled instead: with phi[q] = where the data of qubit q sits,
+// phi starts as the product Q of all runs applied to the input, and each run
+// met on the way turns phi into phi o pi^-1, ending at the identity.  The
+// gates keep their order and matrices; only their qubits move.  Taken only
+// when Q is an involution (the permutation pass works in place on those).
+// Returns Q, or an empty vector (nothing changed).
+std::vector<int> swaps_to_front(std::vector<Gate> &gates, const std::vector<int> &run_of,
+                                const std::vector<std::vector<int>> &perms, int M) {
+    if (perms.empty()) return {};
+    std::vector<int> Q(M);
+    for (int q = 0; q < M; ++q) Q[q] = q;
+    for (const std::vector<int> &pi : perms)
+        for (int q = 0; q < M; ++q) Q[q] = pi[Q[q]];
+    for (int q = 0; q < M; ++q)
+        if (Q[Q[q]] != q) return {};
+    std::vector<int> phi = Q;
+    std::vector<Gate> out;
+    out.reserve(gates.size());
+    for (size_t gi = 0; gi < gates.size(); ++gi) {
+        const int r = run_of[gi];
+        if (r >= 0) {
+            if (gi == 0 || run_of[gi - 1] != r) {
+                std::vector<int> inv(M), nphi(M);
+                for (int q = 0; q < M; ++q) inv[perms[size_t(r)][q]] = q;
+                for (int q = 0; q < M; ++q) nphi[q] = phi[inv[q]];
+                phi.swap(nphi);
+            }
+            continue;
+        }
+        Gate g = gates[gi];
+        g.t = phi[g.t];
+        g.cmask = 0;
+        for (int c = 0; c < g.nc; ++c) {
+            g.c[c] = phi[g.c[c]];
+            g.cmask |= bit(g.c[c]);
+        }
+        out.push_back(g);
+    }
+    gates.swap(out);
+    return Q;
+}
+
 // Shared-memory wavefronts of one warp access (lane byte addresses, `width`
 // bytes each): the lanes are served in groups that move 128 bytes (32 lanes
 // of 4-byte, 16 of 8-byte, 8 of 16-byte accesses); within a group, the
@@ -736,16 +785,21 @@ PermDesc perm_desc(const std::vector<int> &pi, int M, qsim_prec prec) {
 }
 
 // Greedy grouping of the gates into tile passes of at most 2^b amplitudes.
+// `reserve`: qubits that the first pass's tile holds whatever its gates (the
+// source-order runs of a permutation that pass gathers).
 template <typename T2>
 void plan_tiled(qsim_plan *p, int b_req, std::vector<int> rem, std::vector<TileOp<T2>> &ops,
-                std::vector<unsigned char> &runs) {
+                std::vector<unsigned char> &runs, uint64_t reserve = 0) {
     const int M = p->M;
     const int b = std::min(b_req, M);
     const int L = std::min(b, p->prec == QSIM_C64 ? 5 : 4);
     const int cap = std::min(b - L, kMaxTileHigh);
+    reserve &= ~(bit(L) - 1);
+    if (__builtin_popcountll(reserve) > cap) reserve = 0;
     while (!rem.empty()) {
-        uint64_t defN = 0, defA = 0, high = 0;
-        int nh = 0;
+        uint64_t defN = 0, defA = 0, high = reserve;
+        int nh = __builtin_popcountll(reserve);
+        reserve = 0;
         std::vector<int> take, keep;
         for (int gi : rem) {
             const Gate &g = p->gates[gi];
@@ -1196,11 +1250,18 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
         if (int rc = next_event(p, s)) return rc;
         ++p->timed_execs;
     }
+    // reading a separate source, the first tile pass can apply the front
+    // permutation itself: the permutation pass is skipped
+    const bool absorb = p->jit_gather_k && src != dst && p->steps.size() > 1 && p->steps[0].type == S_PERM;
+    p->last_absorbed = absorb;
     for (const Step &st : p->steps) {
-        if (timed && !first)
+        const size_t si = size_t(&st - p->steps.data());
+        if (timed && si > 0)
             if (int rc = next_event(p, s)) return rc;
-        if (st.type == S_TILE && st.d.round_count > 0) {
-            const size_t si = size_t(&st - p->steps.data());
+        if (absorb && si == 0) continue;
+        if (absorb && si == 1) {
+            if (int rc = launch_jit_pass(p->jit_gather_k, dst, src, p->M, st.d, p->d_runs, s)) return rc;
+        } else if (st.type == S_TILE && st.d.round_count > 0) {
             if (si < p->jit_k.size() && p->jit_k[si]) {
                 if (int rc = launch_jit_pass(p->jit_k[si], dst, first ? src : dst, p->M, st.d, p->d_runs, s)) return rc;
             } else if (int rc = launch_tile_reg(dst, first ? src : dst, p->M, st.d, p->d_regops, p->d_rounds,
@@ -1357,6 +1418,23 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
             std::vector<int> run_of;
             std::vector<std::vector<int>> perms;
             find_swap_runs(p->gates, run_of, perms, M);
+            // all runs as one permutation at the front, when their product allows
+            uint64_t reserve = 0;
+            p->front_perm = swaps_to_front(p->gates, run_of, perms, M);
+            if (!p->front_perm.empty()) {
+                run_of.assign(p->gates.size(), -1);
+                perms.clear();
+                Step st{};
+                st.type = S_PERM;
+                st.perm = perm_desc(p->front_perm, M, prec);
+                st.bytes = 2.0 * std::ldexp(1.0, M) * double(amp_bytes(prec));
+                p->steps.push_back(st);
+                // the first pass's tile holds the qubits of the source's low bits
+                // (so that a specialised first pass can gather the permutation;
+                // general and specialised plans keep the same passes)
+                if (prec == QSIM_C64)
+                    for (int q = 0; q < std::min(5, M); ++q) reserve |= bit(p->front_perm[q]);
+            }
             std::vector<std::vector<int>> segs(1);
             std::vector<int> perm_after;  // perm_after[s] = permutation following segment s, or -1
             for (size_t gi = 0; gi < p->gates.size(); ++gi) {
@@ -1379,7 +1457,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
             if (prec == QSIM_C64) {
                 std::vector<TileOp<float2>> ops;
                 for (size_t si = 0; si < segs.size(); ++si) {
-                    plan_tiled(p, b, segs[si], ops, runs);
+                    plan_tiled(p, b, segs[si], ops, runs, si == 0 ? reserve : 0);
                     add_perm(int(si));
                 }
                 std::vector<RegOp> regops;
@@ -1402,10 +1480,28 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
                             descs.push_back(&p->steps[si].d);
                             at.push_back(si);
                         }
+                    // and the first tile pass once more, gathering the front
+                    // permutation, if its tile covers the source's lowest 4 bits
+                    std::vector<const std::vector<int> *> gathers(descs.size(), nullptr);
+                    bool gather = !p->front_perm.empty() && p->steps.size() > 1 && p->steps[1].type == S_TILE &&
+                                  p->steps[1].d.round_count > 0;
+                    for (int q = 0; gather && q < std::min(4, M); ++q) {
+                        const TilePassDesc &d1 = p->steps[1].d;
+                        const int pq = p->front_perm[q];
+                        bool in = pq < d1.L;
+                        for (int h = 0; h < d1.nh; ++h) in = in || d1.hpos[h] == pq;
+                        gather = in;
+                    }
+                    if (gather) {
+                        descs.push_back(&p->steps[1].d);
+                        gathers.push_back(&p->front_perm);
+                    }
                     std::vector<cudaKernel_t> ks;
-                    if (!descs.empty() && jit_build(descs, regops, rounds, runs, &p->jit_libs, &ks, &p->jit_log) == QSIM_OK) {
+                    if (!descs.empty() &&
+                        jit_build(descs, gathers, regops, rounds, runs, &p->jit_libs, &ks, &p->jit_log) == QSIM_OK) {
                         p->jit_k.assign(p->steps.size(), nullptr);
                         for (size_t j = 0; j < at.size(); ++j) p->jit_k[at[j]] = ks[j];
+                        if (gather) p->jit_gather_k = ks.back();
                     }
                 }
                 p->h_regops = std::move(regops);
@@ -1516,11 +1612,12 @@ int qsim_plan_timing(qsim_plan *p, int64_t n_max, double *ms, double *bytes, int
     const int64_t n = std::min<int64_t>(n_max, int64_t(nst));
     for (int64_t j = 0; j < n; ++j) {
         if (ms) ms[j] = 0.0;
-        if (bytes) bytes[j] = p->steps[j].bytes;
+        const bool skipped = j == 0 && p->last_absorbed;
+        if (bytes) bytes[j] = skipped ? 0.0 : p->steps[j].bytes;
         if (kind) {
             const Step &st = p->steps[j];
             const bool spec = size_t(j) < p->jit_k.size() && p->jit_k[size_t(j)];
-            kind[j] = st.type == S_TILE && st.d.round_count > 0 ? (spec ? 5 : 4) : int32_t(st.type);
+            kind[j] = skipped ? 6 : st.type == S_TILE && st.d.round_count > 0 ? (spec ? 5 : 4) : int32_t(st.type);
         }
     }
     if (p->ev_used > 0) {
@@ -1558,7 +1655,11 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
         if (st.type == S_GATE) {
             add("step %zu GATE t=%d nc=%d kind=%d\n", j, st.g.t, st.g.nc, int(st.g.kind));
         } else if (st.type == S_PERM) {
-            add("step %zu PERM tile_qubits=%d low=%d\n", j, st.perm.ns, st.perm.lb);
+            add("step %zu PERM tile_qubits=%d low=%d%s\n", j, st.perm.ns, st.perm.lb,
+                j == 0 && !p->front_perm.empty()
+                    ? (p->jit_gather_k ? " (swap runs moved to the front; gathered by step 1 when src != dst)"
+                                       : " (swap runs moved to the front)")
+                    : "");
         } else if (st.type == S_FUSED) {
             add("step %zu FUSED k=%d unitary=%d runbits=%d qubits=", j, st.f.k, st.f.unitary, st.f.runbits);
             for (int a = 0; a < st.f.k; ++a) add("%d ", __builtin_ctz(st.f.posA[1 << a]));

@@ -158,7 +158,7 @@ struct RegOp {
     uint8_t tw;          // K_TAB: index bits
     uint16_t smask;      // slots the op touches (pair kinds: the lower slot of each pair)
     uint8_t tpos[12];    // K_TAB: tile-local positions of the index bits (bit j of the entry index)
-    uint8_t cidx[16];    // K_TAB: index contribution of slot c (the slot bits among tpos)
+    uint16_t cidx[16];   // K_TAB: index contribution of slot c (the slot bits among tpos; up to 9 index bits)
     uint32_t nmask;      // tile bits outside the slots that the thread's index must have set
     uint32_t tbn;        // K_DIAG: target bit when it is not a slot qubit (tested on the thread's index)
     uint16_t tsel;       // K_DIAG: slots whose target bit is set (target a slot qubit)
@@ -196,9 +196,12 @@ bool build_register_rounds(const std::vector<TileOp<float2>> &ops, int op_begin,
                            std::vector<unsigned char> &runs);
 // Specialised register passes (jit.cu): generate, compile (NVRTC) and load one
 // kernel per pass; QSIM_EUNSUPPORTED (with *log) when NVRTC is unavailable.
-int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<RegOp> &regops,
-              const std::vector<RoundDesc> &rounds, const std::vector<unsigned char> &runs,
-              std::vector<cudaLibrary_t> *libs, std::vector<cudaKernel_t> *kernels, std::string *log);
+// gathers[i], when present and non-null, is a qubit permutation (an
+// involution) that pass i also applies to its input as it reads it.
+int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector<const std::vector<int> *> &gathers,
+              const std::vector<RegOp> &regops, const std::vector<RoundDesc> &rounds,
+              const std::vector<unsigned char> &runs, std::vector<cudaLibrary_t> *libs,
+              std::vector<cudaKernel_t> *kernels, std::string *log);
 void jit_release(cudaLibrary_t lib);
 void jit_release(const std::vector<cudaLibrary_t> &libs);
 // The persistent trajectory kernel in register rounds ("qs_traj"): passes with

@@ -489,3 +489,31 @@ def test_auto_mode_picks_by_time_model(orc):
         st = qs.State(M).set(x)
         plan.execute(st)
         _close(st.get(), orc.run(M, recs, x128, nthreads=NT), "c64")
+
+
+@pytest.mark.parametrize("specialize", [True, False])
+def test_front_permutation(orc, specialize):
+    """The QFT's closing swap runs become one permutation at the front (the
+    gates after them relabelled).  Out of place, a specialised first pass
+    gathers it while reading the source and the permutation pass is skipped;
+    in place, the permutation pass runs.  Both give the same amplitudes
+    bitwise, and the oracle's within tolerance."""
+    M = 20
+    x, x128 = _input(M, "c64")
+    recs = W.circuit_c2_qft(M, sigma=1e-4)["noisy"]
+    plan = qs.Plan(M, recs, mode="tiled", specialize=specialize)
+    desc = plan.describe()
+    assert "moved to the front" in desc
+    assert ("gathered by step 1" in desc) == specialize
+    src = qs.State(M).set(x)
+    out = qs.State(M)
+    plan.set_timing(True)
+    plan.execute(out, src)
+    _, _, kinds, _ = plan.timing()
+    plan.set_timing(False)
+    assert (kinds[0] == 6) == specialize
+    inp = qs.State(M).set(x)
+    plan.execute(inp)
+    a, b = out.get(), inp.get()
+    assert np.array_equal(a, b)
+    _close(a, orc.run(M, recs, x128, nthreads=NT), "c64")
