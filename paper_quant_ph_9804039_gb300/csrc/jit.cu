@@ -109,6 +109,13 @@ void emit_pairs(Src &out, const RegOp &op, int RB, const char *kind) {
         const int c1 = c | (1 << K);
         if (!std::strcmp(kind, "swap")) {
             out("    { const float2 t = v[%d]; v[%d] = v[%d]; v[%d] = t; }\n", c, c, c1, c1);
+        } else if (!std::strcmp(kind, "nhad")) {
+            const std::string e0 = flit(op.u[0].x), e1 = flit(op.u[1].x), e2 = flit(op.u[2].x), e3 = flit(op.u[3].x);
+            out("    { const float2 a = v[%d], b = v[%d]; "
+                "v[%d] = make_float2(fmaf(%s, a.x, fmaf(%s, b.x, a.x + b.x)), fmaf(%s, a.y, fmaf(%s, b.y, a.y + b.y))); "
+                "v[%d] = make_float2(fmaf(%s, a.x, fmaf(%s, b.x, a.x - b.x)), fmaf(%s, a.y, fmaf(%s, b.y, a.y - b.y))); }\n",
+                c, c1, c, e0.c_str(), e1.c_str(), e0.c_str(), e1.c_str(), c1, e2.c_str(), e3.c_str(), e2.c_str(),
+                e3.c_str());
         } else if (!std::strcmp(kind, "had")) {
             out("    { const float2 a = v[%d], b = v[%d]; v[%d] = make_float2(a.x + b.x, a.y + b.y); "
                 "v[%d] = make_float2(a.x - b.x, a.y - b.y); }\n",
@@ -168,7 +175,9 @@ void emit_op(Src &out, const RegOp &op, const RoundDesc &rd, int RB, const TileP
     if (op.gmask) out("   if ((base & %lluull) == %lluull)\n", (unsigned long long)op.gmask, (unsigned long long)op.gmask);
     if (op.nmask) out("   if ((i0 & %uu) == %uu)\n", op.nmask, op.nmask);
     out("   {\n");
-    if (code >= RC_HAD) {
+    if (code >= RC_NHAD) {
+        emit_pairs(out, op, RB, "nhad");
+    } else if (code >= RC_HAD) {
         emit_pairs(out, op, RB, "had");
     } else if (code < RC_PHASE_ALL) {
         const int fam = code / 8;  // 0 dense, 1 real, 2 swap
@@ -206,8 +215,7 @@ void emit_op(Src &out, const RegOp &op, const RoundDesc &rd, int RB, const TileP
         out(";\n");
         for (int c = 0; c < S; ++c) {
             if (!((op.smask >> c) & 1)) continue;
-            out("    { const float4 t = __ldg(tab + (g | %uu)); v[%d] = qs_cmulx(make_float2(t.x, t.y), "
-                "make_float2(t.z, t.w), v[%d]); }\n",
+            out("    { const float4 t = __ldg(tab + (g | %uu)); v[%d] = qs_cmul(make_float2(t.x, t.y), v[%d]); }\n",
                 unsigned(op.cidx[c]), c, c);
         }
     }

@@ -103,6 +103,21 @@ __device__ __forceinline__ void pairs(Slots<RB> &v, const RegOp &op) {
     }
 }
 
+// A Hadamard with an error, without its factor 1/sqrt 2: (a, b) <- (a + b +
+// e0 a + e1 b, a - b + e2 a + e3 b) on slot bit K.
+template <int RB, int K>
+__device__ __forceinline__ void pairs_nhad(Slots<RB> &v, const RegOp &op) {
+    const float e0 = op.u[0].x, e1 = op.u[1].x, e2 = op.u[2].x, e3 = op.u[3].x;
+#pragma unroll
+    for (int c = 0; c < (1 << RB); ++c) {
+        if (c & (1 << K)) continue;
+        const int c1 = c | (1 << K);
+        const float2 a = v.x[c], b = v.x[c1];
+        v.x[c] = make_float2(fmaf(e0, a.x, fmaf(e1, b.x, a.x + b.x)), fmaf(e0, a.y, fmaf(e1, b.y, a.y + b.y)));
+        v.x[c1] = make_float2(fmaf(e2, a.x, fmaf(e3, b.x, a.x - b.x)), fmaf(e2, a.y, fmaf(e3, b.y, a.y - b.y)));
+    }
+}
+
 // Hadamard without its factor: (a, b) <- (a + b, a - b) on slot bit K.
 template <int RB, int K>
 __device__ __forceinline__ void pairs_had(Slots<RB> &v) {
@@ -163,8 +178,8 @@ __device__ __forceinline__ void apply_op(Slots<RB> &v, const RegOp &op, uint32_t
 #pragma unroll
         for (int c = 0; c < S; ++c) {
             if (!((sm >> c) & 1u)) continue;
-            const float4 t = __ldg(tab + (g | op.cidx[c]));
-            v.x[c] = cmulx(make_float2(t.x, t.y), make_float2(t.z, t.w), v.x[c]);
+            const float4 t = __ldg(tab + (g | op.cidx[c]));  // unit-modulus float entry (the lo part unused)
+            v.x[c] = cmul(make_float2(t.x, t.y), v.x[c]);
         }
         return;
     }
@@ -283,7 +298,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_tile_reg(float2 *dst, const flo
                         case 0: pairs_had<RB, 0>(v); break;
                         case 1: pairs_had<RB, 1>(v); break;
                         case 2: pairs_had<RB, 2>(v); break;
-                        default: if constexpr (RB > 3) pairs_had<RB, 3>(v); break;
+                        case 3: if constexpr (RB > 3) pairs_had<RB, 3>(v); break;
+                        case 4: pairs_nhad<RB, 0>(v, op); break;
+                        case 5: pairs_nhad<RB, 1>(v, op); break;
+                        case 6: pairs_nhad<RB, 2>(v, op); break;
+                        default: if constexpr (RB > 3) pairs_nhad<RB, 3>(v, op); break;
                     }
                     continue;
                 }

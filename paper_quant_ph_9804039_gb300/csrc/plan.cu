@@ -169,6 +169,37 @@ TileOp<T2> make_tile_op(const Gate &g, const int *loc, uint64_t S) {
 // precedes an uncontrolled dense gate on local target tl: entry
 // (idx << 1) | target bit, idx over the local bits tpos[0..tw).  FP64
 // products, stored as float hi + lo (complex64) or double (complex128).
+// Float parts (re, im) of a phase factor f for kernels that multiply by them
+// alone (no lo part): among the floats within two ulps of f's components, the
+// pair whose squared modulus is closest to |f|^2 (then the nearest).  A
+// table entry is then unit-modulus to ~1e-9 instead of ~1e-7, so that
+// repeated multiplications do not drift the norm; its angle moves by at most
+// two ulps (~2e-7 rad), an error that is unbiased over the entries.
+void unit_hi(double fr, double fi, float *re, float *im) {
+    const double m2 = fr * fr + fi * fi;
+    float br = float(fr), bi = float(fi);
+    double bcost = std::fabs(double(br) * br + double(bi) * bi - m2);
+    double bdist = (double(br) - fr) * (double(br) - fr) + (double(bi) - fi) * (double(bi) - fi);
+    float cr = float(fr);
+    for (int k = 0; k < 2; ++k) cr = std::nextafter(cr, -INFINITY);
+    for (int a = -2; a <= 2; ++a, cr = std::nextafter(cr, INFINITY)) {
+        float ci = float(fi);
+        for (int k = 0; k < 2; ++k) ci = std::nextafter(ci, -INFINITY);
+        for (int b = -2; b <= 2; ++b, ci = std::nextafter(ci, INFINITY)) {
+            const double cost = std::fabs(double(cr) * cr + double(ci) * ci - m2);
+            const double dist = (double(cr) - fr) * (double(cr) - fr) + (double(ci) - fi) * (double(ci) - fi);
+            if (cost < bcost || (cost == bcost && dist < bdist)) {
+                bcost = cost;
+                bdist = dist;
+                br = cr;
+                bi = ci;
+            }
+        }
+    }
+    *re = br;
+    *im = bi;
+}
+
 template <typename T2>
 uint32_t add_pre_table(std::vector<unsigned char> &runs, const std::vector<Gate> &gates, const std::vector<int> &run,
                        const int *loc, int tl, const int *tpos, int tw, bool *one0) {
@@ -197,8 +228,9 @@ uint32_t add_pre_table(std::vector<unsigned char> &runs, const std::vector<Gate>
         unsigned char *dst = runs.data() + start + size_t(e) * esz;
         if constexpr (sizeof(T2) == 8) {
             float v[4];
-            split_f(fr, v[0], v[2]);
-            split_f(fi, v[1], v[3]);
+            unit_hi(fr, fi, &v[0], &v[1]);
+            v[2] = float(fr - double(v[0]));
+            v[3] = float(fi - double(v[1]));
             std::memcpy(dst, v, 16);
         } else {
             const double v[2] = {fr, fi};
@@ -485,7 +517,7 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
                     for (int k2 = 0; k2 < RB; ++k2)
                         if ((c >> k2) & 1) dep |= 1u << rd.pos[k2];
                     const double ang = 2.0 * M_PI * double(Q[dep]) / 4294967296.0;
-                    f[c] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+                    unit_hi(std::cos(ang), std::sin(ang), &f[c].x, &f[c].y);
                 }
                 const size_t start = (runs.size() + 15) & ~size_t(15);
                 runs.resize(start + sizeof(f), 0);
@@ -517,9 +549,32 @@ bool build_rounds(const std::vector<TileOp<float2>> &ops, int op_begin, int op_c
                     pscale *= double(op.u[0].x) + double(op.ul[0].x);
                     ++nhad;
                 }
+                // a Hadamard with an error, O = (H + E) / sqrt 2, |E| small: the
+                // sums a +- b carry H, E enters as two FMA per component (its
+                // entries are ~1e-4, so their float rounding is ~1e-11 absolute)
+                bool near_had = false;
+                if (!had && op.kind == K_RDENSE && partial == 0 && op.nmask == 0 && op.gmask == 0 && nhad < 64) {
+                    const double sgn[4] = {1.0, 1.0, 1.0, -1.0};
+                    double e[4];
+                    near_had = true;
+                    for (int j = 0; j < 4; ++j) {
+                        e[j] = (double(op.u[j].x) + double(op.ul[j].x)) * M_SQRT2 - sgn[j];
+                        near_had = near_had && std::fabs(e[j]) < 1.0 / 64;
+                    }
+                    if (near_had) {
+                        for (int j = 0; j < 4; ++j) {
+                            op.u[j] = make_float2(float(e[j]), 0.f);
+                            op.ul[j] = make_float2(0.f, 0.f);
+                        }
+                        pscale *= M_SQRT1_2;
+                        ++nhad;
+                    }
+                }
                 switch (op.kind) {
                     case K_DENSE: op.code = uint8_t(RC_DENSE + partial + op.k); break;
-                    case K_RDENSE: op.code = uint8_t((had ? RC_HAD : RC_RDENSE + partial) + op.k); break;
+                    case K_RDENSE:
+                        op.code = uint8_t((had ? RC_HAD : near_had ? RC_NHAD : RC_RDENSE + partial) + op.k);
+                        break;
                     case K_SWAPX: op.code = uint8_t(RC_SWAP + partial + op.k); break;
                     case K_PHASE1: op.code = op.smask == all_slots ? RC_PHASE_ALL : RC_PHASE; break;
                     case K_DIAG: op.code = RC_DIAG; break;
@@ -1189,11 +1244,12 @@ int count_fused_blocks(const std::vector<Gate> &gates, int k) {
 double regop_cost(const RegOp &op, int S) {
     const double touched = double(__builtin_popcount(op.smask)) / double(S) / double(1u << __builtin_popcount(op.nmask));
     const int c = op.code;
+    if (c >= RC_NHAD) return 6.0;
     if (c >= RC_HAD) return 2.0;
     if (c < RC_RDENSE) return 16.0 * touched * 2.0;  // pair kinds: smask counts pairs
     if (c < RC_SWAP) return 8.0 * touched * 2.0;
     if (c < RC_PHASE_ALL) return 0.5;
-    if (c == RC_TAB) return 10.0 * touched;
+    if (c == RC_TAB) return 6.0 * touched;
     if (c == RC_PHRUN) return 24.0;
     return 8.0 * touched;
 }
@@ -1679,7 +1735,8 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
                 for (int k = 0; k < rd.op_count; ++k) {
                     const RegOp &op = p->h_regops[size_t(st.d.op_begin + rd.op_begin + k)];
                     const int c = op.code;
-                    if (c >= RC_HAD) add(" HAD/%d", c - RC_HAD);
+                    if (c >= RC_NHAD) add(" NHAD/%d", c - RC_NHAD);
+                    else if (c >= RC_HAD) add(" HAD/%d", c - RC_HAD);
                     else if (c < RC_PHASE_ALL) add(" %s%s/%d", kinds[c / 8], (c & 4) ? "p" : "", c & 3);
                     else if (c == RC_PHASE_ALL || c == RC_PHASE) add(" PHASE");
                     else if (c == RC_DIAG) add(" DIAG");

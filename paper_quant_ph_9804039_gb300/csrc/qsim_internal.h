@@ -178,6 +178,8 @@ enum RegCode : uint8_t {
     RC_TAB = 28,
     RC_PHRUN = 29,
     RC_HAD = 32,      // + k: uncontrolled c [[1, 1], [1, -1]], the factor c deferred to the end of the pass
+    RC_NHAD = 36,     // + k: uncontrolled real O = (H + E) / sqrt 2 with E small (a Hadamard with an error):
+                      // (a + b + e00 a + e01 b, a - b + e10 a + e11 b) with e_j in u[j].x, 1/sqrt 2 deferred
 };
 static_assert(sizeof(RegOp) % 16 == 0, "RegOp is copied in 16-byte units");
 struct RoundDesc {
