@@ -98,8 +98,10 @@ typedef struct qsim_opts {
 /* Counts describing one execution of a plan. */
 typedef struct qsim_plan_stats {
     int64_t n_gates;       /* gate records in the circuit */
-    int64_t n_passes;      /* passes over the whole state vector */
-    int64_t n_launches;    /* kernel launches per execution */
+    int64_t n_passes;      /* passes over the whole state vector (an in-place execution) */
+    int64_t n_launches;    /* kernel launches per in-place execution; an out-of-place execution whose
+                            * first specialised pass gathers the front permutation (see
+                            * qsim_plan_execute) launches one fewer */
     int32_t mode;          /* the mode actually used */
     int32_t tile_bits;     /* tile size used (QSIM_MODE_TILED) */
     int32_t fuse_k;        /* block width used (QSIM_MODE_FUSED) */
@@ -140,6 +142,16 @@ int qsim_reset(qsim_state *st);
  * on_device != 0).  Host copies wait for the state's stream. */
 int qsim_set_state(qsim_state *st, const void *amps, int on_device);
 
+/* As qsim_set_state, but only queues the copy on the state's stream and
+ * returns (outside the paper; for pipelines that copy the next input while
+ * the current one is being simulated).  Host memory should be page-locked
+ * (cudaHostAlloc / pinned) for the copy to run asynchronously, and `amps` must
+ * stay unchanged until the state's stream has passed the copy: until a later
+ * call that waits for the state (qsim_get_state, qsim_fidelity, ...) or a
+ * stream synchronisation.  Work queued on the state afterwards, on any
+ * stream, is ordered after the copy as usual. */
+int qsim_set_state_async(qsim_state *st, const void *amps, int on_device);
+
 /* Copy the 2^M amplitudes out to `amps` (host, or device if on_device != 0).
  * Host copies wait for the state's stream. */
 int qsim_get_state(const qsim_state *st, void *amps, int on_device);
@@ -173,7 +185,11 @@ int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n,
 
 /* dst := circuit(src).  src == NULL or src == dst runs in place; otherwise
  * src is left untouched (same M and precision).  Runs on dst's stream after
- * src's queued work. */
+ * src's queued work.  In QSIM_MODE_TILED, runs of SWAP gates (each three
+ * CNOTs) are planned as one qubit permutation at the front of the circuit,
+ * the later gates relabelled; when that permutation is an involution and the
+ * plan is specialised, an out-of-place execution applies it inside the first
+ * pass's reads instead of a separate permutation pass. */
 int qsim_plan_execute(const qsim_plan *plan, qsim_state *dst, const qsim_state *src);
 
 int qsim_plan_stats_get(const qsim_plan *plan, qsim_plan_stats *out);
@@ -203,7 +219,9 @@ int qsim_plan_set_timing(qsim_plan *plan, int enable);
  * of one execution: ms[j] = milliseconds summed over the timed executions,
  * bytes[j] = algorithmic bytes of that launch, kind[j] = 0 single gate,
  * 1 shared-memory tile pass, 2 fused block, 3 qubit permutation pass,
- * 4 register tile pass (complex64), 5 specialised register tile pass.
+ * 4 register tile pass (complex64), 5 specialised register tile pass,
+ * 6 a permutation pass left out by the last execution (the next pass gathered
+ * it; no launch, bytes 0).
  * *executions = number of timed executions.
  * Any output array may be NULL.  Clears the record. */
 int qsim_plan_timing(qsim_plan *plan, int64_t n_max, double *ms, double *bytes, int32_t *kind,

@@ -97,6 +97,7 @@ SIGNATURES = [
     ("qsim_state_info", ctypes.c_int, [_vp, _ip, _ip, ctypes.POINTER(_vp)]),
     ("qsim_reset", ctypes.c_int, [_vp]),
     ("qsim_set_state", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    ("qsim_set_state_async", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     ("qsim_get_state", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     ("qsim_copy_state", ctypes.c_int, [_vp, _vp]),
     ("qsim_apply_gate", ctypes.c_int, [_vp, _dp, ctypes.c_int, _ip, ctypes.c_int]),
@@ -239,6 +240,16 @@ class State:
             a = np.ascontiguousarray(amps, dtype=np.complex64 if self.prec == QSIM_C64 else np.complex128)
             assert a.size == (1 << self.M)
             _check(_lib.qsim_set_state(self._h, _vp(a.ctypes.data), 0))
+        return self
+
+    def set_async(self, amps):
+        """Queue a copy in from a pinned host tensor (or a CUDA tensor) on this
+        state's stream and return (qsim_set_state_async); `amps` must stay
+        unchanged until later work that waits for this state."""
+        torch = _torch()
+        assert isinstance(amps, torch.Tensor) and amps.dtype == self.tensor.dtype and amps.is_contiguous()
+        assert amps.numel() == (1 << self.M) and (amps.is_cuda or amps.is_pinned())
+        _check(_lib.qsim_set_state_async(self._h, _vp(amps.data_ptr()), 1 if amps.is_cuda else 0))
         return self
 
     def get(self) -> np.ndarray:

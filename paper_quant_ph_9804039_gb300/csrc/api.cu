@@ -175,14 +175,25 @@ int qsim_reset(qsim_state *st) {
     return launch_zero_state(st->amps, st->M, st->prec, st->stream);
 }
 
+static int copy_in(void *dst, const void *src, size_t bytes, bool on_device, cudaStream_t s) {
+    QS_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return QSIM_OK;
+}
+
 int qsim_set_state(qsim_state *st, const void *amps, int on_device) {
     if (int rc = check_state(st)) return rc;
     if (!amps) { set_error("amps is NULL"); return QSIM_EINVAL; }
     const size_t bytes = (size_t(1) << st->M) * amp_bytes(st->prec);
-    QS_CUDA(cudaMemcpyAsync(st->amps, amps, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            st->stream));
+    if (int rc = copy_in(st->amps, amps, bytes, on_device != 0, st->stream)) return rc;
     if (!on_device) QS_CUDA(cudaStreamSynchronize(st->stream));
     return QSIM_OK;
+}
+
+int qsim_set_state_async(qsim_state *st, const void *amps, int on_device) {
+    if (int rc = check_state(st)) return rc;
+    if (!amps) { set_error("amps is NULL"); return QSIM_EINVAL; }
+    const size_t bytes = (size_t(1) << st->M) * amp_bytes(st->prec);
+    return copy_in(st->amps, amps, bytes, on_device != 0, st->stream);
 }
 
 int qsim_get_state(const qsim_state *st, void *amps, int on_device) {

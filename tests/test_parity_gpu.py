@@ -517,3 +517,26 @@ def test_front_permutation(orc, specialize):
     a, b = out.get(), inp.get()
     assert np.array_equal(a, b)
     _close(a, orc.run(M, recs, x128, nthreads=NT), "c64")
+
+
+def test_set_state_async_orders_with_later_work(orc):
+    """qsim_set_state_async queues the host copy on the state's own stream and
+    returns; a plan executed from that state on another stream runs after the
+    copy (cross-stream event), and gives the synchronous copy's result."""
+    torch = pytest.importorskip("torch")
+    M = 18
+    x, x128 = _input(M, "c64")
+    recs = W.circuit_c2_qft(M, sigma=1e-4)["noisy"]
+    plan = qs.Plan(M, recs, mode="tiled", specialize=True)
+    h = torch.empty(1 << M, dtype=torch.complex64, pin_memory=True)
+    h.numpy()[:] = x
+    copy_stream = torch.cuda.Stream()
+    src = qs.State(M, stream=copy_stream, zero=False)
+    out = qs.State(M)
+    src.set_async(h)
+    plan.execute(out, src)
+    got = out.get()
+    ref = qs.State(M)
+    plan.execute(ref, qs.State(M).set(x))
+    assert np.array_equal(got, ref.get())
+    _close(got, orc.run(M, recs, x128, nthreads=NT), "c64")
