@@ -711,6 +711,34 @@ int find_swap_runs(const std::vector<Gate> &g, std::vector<int> &run_of, std::ve
     return nrun;
 }
 
+// The deferred Hadamard factors of the register passes (a scalar, which
+// commutes with every later op and permutation) are carried forward and
+// applied once, compensated, by the last register pass of the plan, instead
+// of once per pass.  Amplitudes grow meanwhile; a pass applies what it
+// carries as soon as the carried factor falls below 2^-24 (so a normalised
+// state stays below 2^56 inside any pass).
+void carry_pass_scales(std::vector<Step> &steps) {
+    double carry = 1.0;
+    Step *last = nullptr;
+    for (Step &st : steps) {
+        if (st.type != S_TILE || st.d.round_count == 0) continue;
+        last = &st;
+        if (st.d.pscale_on) carry *= double(st.d.pscale_hi) + double(st.d.pscale_lo);
+        st.d.pscale_on = 0;
+        if (carry < std::ldexp(1.0, -24)) {
+            st.d.pscale_on = 1;
+            st.d.pscale_hi = float(carry);
+            st.d.pscale_lo = float(carry - double(st.d.pscale_hi));
+            carry = 1.0;
+        }
+    }
+    if (last && carry != 1.0) {
+        last->d.pscale_on = 1;
+        last->d.pscale_hi = float(carry);
+        last->d.pscale_lo = float(carry - double(last->d.pscale_hi));
+    }
+}
+
 // Every swap run moved to the front of the circuit.  A run that exchanges
 // qubit positions (pi[q] = new position of q) can be left out if every later
 // gate is relabelled instead: with phi[q] = where the data of qubit q sits,
@@ -1525,6 +1553,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
                     TilePassDesc d = st.d;
                     if (build_rounds(ops, st.d.op_begin, st.d.op_count, d, RB, regops, rounds, runs)) st.d = d;
                 }
+                carry_pass_scales(p->steps);
                 rc = upload(p, &p->d_ops, ops.data(), ops.size() * sizeof(ops[0]), &p->ops_bytes);
                 if (rc == QSIM_OK) rc = upload(p, &p->d_regops, regops.data(), regops.size() * sizeof(RegOp), &p->regops_bytes);
                 if (rc == QSIM_OK) rc = upload(p, &p->d_rounds, rounds.data(), rounds.size() * sizeof(RoundDesc), &p->rounds_bytes);
