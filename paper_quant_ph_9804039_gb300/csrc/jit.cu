@@ -6,11 +6,14 @@
 // its instruction stream.  Here every register tile pass of a plan becomes its
 // own kernel, generated as CUDA source at plan creation with the pass's tile
 // layout, rounds, op kinds, slot masks and matrix entries as literals, and
-// compiled by NVRTC for sm_103a into one cubin per plan.  The arithmetic is
-// that of the general kernel (Section 2.1's pair update with compensated
-// entries; runs of phase gates as one phase polynomial), op by op in the same
-// order, so results are bitwise those of the general kernel up to the
-// compiler's scheduling of independent operations.  NVRTC is loaded with
+// compiled by NVRTC for sm_103a, one program per pass on a pool of host
+// threads.  The kernel also stages its tiles through shared memory with
+// cp.async (the next tile in flight) and may gather a qubit permutation on
+// the way in (see emit_pass).  The arithmetic is that of the general kernel
+// (Section 2.1's pair update with compensated entries, unit-modulus phase
+// tables, Hadamards with the factor deferred; runs of phase gates as one
+// phase polynomial), op by op in the same order, so results are bitwise
+// those of the general kernel.  NVRTC is loaded with
 // dlopen on first use; without it, or if compilation fails, the plan keeps the
 // general kernel (qsim_plan_describe says which).
 #include <dlfcn.h>

@@ -10,9 +10,10 @@
 // amplitude however many gates it holds; the first round of a pass reads
 // device memory and the last writes it, and shared memory carries the tile
 // between rounds.  Runs of phase gates on tile qubits are one table lookup
-// per amplitude (K_TAB), longer runs that reach outside the tile a phase
-// polynomial (K_PHRUN).  Gate entries are hi + lo floats (compensated
-// complex64, see cx.cuh).
+// per amplitude (K_TAB: unit-modulus float entries, one complex multiply),
+// longer runs that reach outside the tile a phase polynomial (K_PHRUN).
+// Other gate entries are hi + lo floats (compensated complex64, see cx.cuh);
+// Hadamards, exact or with a small error, defer their 1/sqrt 2.
 #include "cx.cuh"
 #include "qsim_internal.h"
 #include "tile_ops.cuh"
