@@ -64,3 +64,25 @@ def test_single_rank_defaults():
         assert bench.job_throughput(2e9, 1, 4.0) == 2e9 / 4e-3
     finally:
         os.environ.update(env)
+
+
+def test_clock_sampler_summary():
+    """The clocks record of a bench line: median SM clock over the samples
+    taken inside the timed region only, the maximum clock, and every throttle
+    reason that was Active in any of them."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cs = bench.ClockSampler(0)
+    cs.lines = [
+        "1200, 2070, 300.0, 0x0, Not Active, Active, Not Active, Not Active",  # before the region
+        "2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2055, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+    ]
+    cs.start = 1
+    s = cs.summary()
+    assert s["samples"] == 3
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]  # the hw_thermal line before the region is not counted
+    empty = bench.ClockSampler(0)
+    assert empty.summary()["reasons"] == ["unavailable"]
