@@ -77,3 +77,9 @@ def test_invalid_arguments_rejected_on_host():
     g["U"][0][0] = 1.0
     assert lib.qsim_plan_create(4, 0, ctypes.c_void_p(g.ctypes.data), 1, ctypes.byref(o),
                                 ctypes.byref(h)) == qs.QSIM_EINVAL
+
+
+def test_async_copy_rejects_null_on_host():
+    lib = qs.load_library()
+    assert lib.qsim_set_state_async(None, None, 0) == qs.QSIM_EINVAL
+    assert b"NULL" in lib.qsim_last_error()
