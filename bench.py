@@ -1,12 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the error-injecting state-vector simulator on GB300.
 
-Workload (default): the quantum-FFT circuit on M=28 qubits, complex64
-(2 GiB per state vector): H + controlled-R_k ladder (406 gates) + 14
-bit-reversal swaps, Gaussian phase error sigma=1e-4 per gate, applied to a
-random normalised complex Gaussian input.  One step = the error-free circuit
-and the noisy circuit, both from the resident input state, then the fidelity
-|<ideal|noisy>|^2 and the noisy norm read back to the host.
+Workload (default): the 33-qubit brickwork, complex64, both state vectors
+resident (2 x 64 GiB): 24 layers of a Haar-random SU(2) on every qubit and
+CNOTs on alternating neighbour pairs, a Toffoli on a random triple after
+every 4th layer (1182 gates), every gate over-rotated by a Gaussian angle
+(sigma = 1e-3).  One step = both states reset to |0...0>, the error-free and
+the noisy circuit applied in place, then the fidelity |<ideal|noisy>|^2 and
+the noisy norm read back to the host.  The plans are made in the library's
+AUTO mode (the execution form is chosen when the plan is made); the fused
+tensor-core, tiled and one-gate-per-launch forms are each timed beside it.
+
+Extra keys: the M=28 quantum FFT (the tiled register passes' workload), one
+dense gate per launch at M=30, batched error trajectories (M=16, T=4096),
+the served request stream, and the CPU oracle on a bounded sample.
 
 metric: amplitude-updates/s = (logical gates applied) * 2^M / second, summed
 over ranks.  Per-launch CUDA events (recorded by the library on the launching
@@ -20,6 +27,7 @@ on the data path: the per-rank work is fixed, weak scaling).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -35,34 +43,46 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 WORKLOADS = {
-    "qft-m28-c64": dict(M=28, sigma=1e-4),
-    # smaller case of the same circuit for ncu captures (512 MiB per state, > L2)
-    "qft-m26-c64": dict(M=26, sigma=1e-4),
     # 33-qubit brickwork (24 layers, Haar SU(2) + CNOT, Toffoli every 4th layer,
-    # over-rotation sigma=1e-3), both states resident (128 GiB): tiled, fused and
-    # one-gate-per-launch forms compared (run on its own: minutes per mode)
-    "brickwork-m33-c64": dict(M=33, sigma=1e-3),
+    # over-rotation sigma=1e-3) from |0...0>, both states resident (128 GiB)
+    "brickwork-m33-c64": dict(M=33, sigma=1e-3, circuit="brickwork"),
+    # the same circuit at M=26 (512 MiB per state, > L2) for ncu captures
+    "brickwork-m26-c64": dict(M=26, sigma=1e-3, circuit="brickwork"),
+    # quantum FFT on M=28 qubits from a random normalised input
+    "qft-m28-c64": dict(M=28, sigma=1e-4, circuit="qft"),
+    # smaller case of the same circuit for ncu captures (512 MiB per state, > L2)
+    "qft-m26-c64": dict(M=26, sigma=1e-4, circuit="qft"),
 }
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 4 for the 33-qubit brickwork, 40 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="qft-m28-c64", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="tiled", choices=["auto", "tiled", "unfused", "fused"])
+    ap.add_argument("--workload", default="brickwork-m33-c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default=None, choices=["auto", "tiled", "unfused", "fused"],
+                    help="execution form of the headline (default: auto for the brickwork, tiled for the QFT)")
+    ap.add_argument("--modes", default="fused,tiled,unfused",
+                    help="brickwork: the forms timed beside the headline")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--no-specialize", action="store_true",
                     help="keep the general register kernel instead of one generated kernel per tile pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-qft", action="store_true", help="brickwork: skip the M=28 quantum-FFT key")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the single-gate, batched-trajectory and serving measurements")
     ap.add_argument("--serve-requests", type=int, default=2000)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 4 if WORKLOADS[a.workload]["M"] >= 30 else 40
+    if a.mode is None:
+        a.mode = "auto" if WORKLOADS[a.workload]["circuit"] == "brickwork" else "tiled"
+    return a
 
 
 # ------------------------------------------------------------------ ranks ---
@@ -185,88 +205,68 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# ------------------------------------------------------------ cpu baseline ---
-def oracle_sample(M, gates, x, budget_s: float, min_gates: int = 3):
-    """Time the CPU oracle (all host threads) on the first gates of the noisy
-    circuit at the full size M, for about budget_s seconds.  Returns
-    (amp-updates/s, gates applied, seconds, threads)."""
-    import oracle
-    orc = oracle.Oracle()
-    nt = oracle.default_threads()
-    psi = x.astype(np.complex128)
-    t0 = time.perf_counter()
-    n = 0
-    while n < len(gates) and (n < min_gates or time.perf_counter() - t0 < budget_s):
-        orc.apply_circuit(psi, gates[n:n + 1], nthreads=nt)
-        n += 1
-    dt = time.perf_counter() - t0
-    return n * float(1 << M) / dt, n, dt, nt
+# GB300: 152 SMs, 128 FP32 lanes per SM, one FMA (2 flop) per lane per clock.
+GB300_SMS, FP32_LANES_PER_SM = 152, 128
 
 
-# ---------------------------------------------------------------- ours ---
-def run_ours(args, rank, world, local):
-    import torch
+def derived_fp32_peak(sm_mhz: float) -> float:
+    """FP32 FMA peak in flop/s derived from the unit counts and an SM clock."""
+    return GB300_SMS * FP32_LANES_PER_SM * 2.0 * sm_mhz * 1e6
 
-    import paper_quant_ph_9804039_gb300 as qs
-    from workloads import generators as W
 
-    wl = WORKLOADS[args.workload]
-    M = wl["M"]
-    c = W.circuit_c2_qft(M, sigma=wl["sigma"])
-    n_logical = c["n_logical_gates"]
-    x = W.random_state(M, seed=2)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.set_stream(stream)
-    xin = qs.State(M, device=dev, stream=stream, zero=False).set(x)
-    ideal = qs.State(M, device=dev, stream=stream, zero=False)
-    noisy = qs.State(M, device=dev, stream=stream, zero=False)
-    mode = args.mode
-    spec = not args.no_specialize
-    t_plan = time.perf_counter()
-    p_ideal = qs.Plan(M, c["ideal"], mode=mode, tile_bits=args.tile_bits, specialize=spec)
-    p_noisy = qs.Plan(M, c["noisy"], mode=mode, tile_bits=args.tile_bits, specialize=spec)
-    t_plan = time.perf_counter() - t_plan
-    specialised = "specialised" in p_noisy.describe()
-    st_i, st_n = p_ideal.stats(), p_noisy.stats()
-    amp_updates_step = 2.0 * n_logical * float(1 << M)
+# plan timing kinds (qsim_plan_timing) -> kernel names
+KIND_NAME = {0: "k_gate (one gate per launch)", 1: "k_tile_pass", 2: "k_fused_tc", 3: "k_permute",
+             4: "k_tile_reg", 5: "qs_pass (specialised register tile pass)", 6: "none (gathered permutation)"}
+KIND_KEY = {0: "k_gate", 1: "k_tile_pass", 2: "k_fused_tc", 3: "k_permute", 4: "k_tile_reg", 5: "qs_pass"}
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 
-    def step():
-        p_ideal.execute(ideal, xin)
-        p_noisy.execute(noisy, xin)
-        return qs.fidelity(ideal, noisy)
 
-    for _ in range(args.warmup):
-        F, nrm = step()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    p_ideal.set_timing(True)
-    p_noisy.set_timing(True)
-    barrier(world)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            F, nrm = step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    barrier(world)
-    p_ideal.set_timing(False)
-    p_noisy.set_timing(False)
-    ms = e0.elapsed_time(e1) / args.steps
-    ms = max_over_ranks(ms, world)
-    value = job_throughput(amp_updates_step, world, ms)
+def _src_sha16(paths) -> str:
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
-    # dominant kernel: per-launch event times of both plans
+
+def profiled_traffic(kernel: str, M: int):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary, scaled from the captured state size to 2^M amplitudes (each of
+    these passes moves every amplitude once, so its traffic is proportional to
+    2^M).  None when there is no capture or the kernel's source changed since
+    it was taken.  Returns (bytes or None, where from, tensor-pipe % or None)."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None, "no ncu capture", None
+    with open(PROFILE_TRAFFIC) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            fld = line.split()
+            # kernel workload M launches dram_bytes_per_launch tensor_pipe_pct sources sha16
+            if fld[0] != kernel:
+                continue
+            if _src_sha16(fld[6].split(",")) != fld[7]:
+                return None, f"kernel source changed since the ncu capture ({fld[1]})", None
+            shift = M - int(fld[2])
+            tensor = None if fld[5] == "-" else float(fld[5])
+            return float(fld[4]) * 2.0 ** shift, f"ncu {fld[1]}, {fld[3]} launches, scaled by 2^{shift}", tensor
+    return None, "no ncu capture", None
+
+
+def plan_roofline(plans, ms_step, steps, M):
+    """Roofline of the dominant kernel of the timed plans from the library's
+    per-launch CUDA events (qsim_plan_timing, recorded on the launching
+    stream): algorithmic bytes per launch over the average launch time,
+    against the measured copy bandwidth."""
     kinds = {}
-    launches_step = 2  # the overlap reduction's two kernels
+    launches_step = 0
     bytes_step = 0.0
-    plan_launches = []
-    for p in (p_ideal, p_noisy):
+    per_plan_launches = []
+    for p in plans:
         t_ms, t_bytes, t_kind, execs = p.timing()
-        plan_launches.append(int(np.sum(t_kind != 6)))  # 6: a permutation gathered by the next pass, no launch
-        launches_step += plan_launches[-1]
+        nl = int(np.sum(t_kind != 6))  # 6: a permutation gathered by the next pass, no launch
+        per_plan_launches.append(nl)
+        launches_step += nl
         bytes_step += float(np.sum(t_bytes))
         for j in range(len(t_ms)):
             k = int(t_kind[j])
@@ -276,35 +276,288 @@ def run_ours(args, rank, world, local):
             d[0] += t_ms[j]
             d[1] += t_bytes[j] * execs
             d[2] += execs
-    kname = {0: "k_gate (one gate per launch)", 1: "k_tile_pass", 2: "k_fused_tc", 3: "k_permute",
-             4: "k_tile_reg", 5: "qs_pass (specialised register tile pass)", 6: "none (gathered permutation)"}
     top = max(kinds, key=lambda k: kinds[k][0])
     tot_ms, tot_bytes, n_launch = kinds[top]
     peak, peak_src = measured_peaks()
     achieved = tot_bytes / (tot_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": kname[top], "achieved": round(achieved, 1), "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "launches_timed": n_launch,
-                "avg_launch_ms": round(tot_ms / max(1, n_launch), 4),
-                "kernel_share_of_step": round(tot_ms / (ms * args.steps), 4)}
+    traffic, t_src, tensor = profiled_traffic(KIND_KEY.get(top, "?"), M)
+    roof = {"bound": "hbm", "kernel": KIND_NAME[top], "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic, "traffic_source": t_src,
+            "algo_bytes_per_launch": tot_bytes / max(1, n_launch), "launches_timed": n_launch,
+            "avg_launch_ms": round(tot_ms / max(1, n_launch), 4),
+            "kernel_share_of_step": round(tot_ms / (ms_step * steps), 4)}
+    if top == 2:
+        roof["tensor_pipe_active_pct_ncu"] = tensor
+    return roof, launches_step, bytes_step, per_plan_launches
 
+
+# ------------------------------------------------------------ cpu baseline ---
+def _host_available_bytes() -> int:
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
+def oracle_size(M: int) -> int:
+    """The largest qubit count <= M whose complex128 state fits in a third of
+    the host's free memory (the oracle runs at the workload's own M when it
+    fits)."""
+    avail = _host_available_bytes()
+    m = M
+    while m > 20 and (16 << m) * 3 > avail:
+        m -= 1
+    return m
+
+
+def oracle_sample(M, gates, x, budget_s: float, min_gates: int = 3):
+    """Time the CPU oracle (all host threads) on the first gates of the noisy
+    circuit, at the workload's M if the host has the memory (else the largest
+    M that fits), for about budget_s seconds after one untimed gate (which
+    touches every page of the state).  Returns (amp-updates/s, gates applied,
+    seconds, threads, M used)."""
+    import oracle
+    orc = oracle.Oracle()
+    nt = oracle.default_threads()
+    Ms = oracle_size(M)
+    if x is not None and Ms == M:
+        psi = x.astype(np.complex128)
+    else:
+        psi = np.zeros(1 << Ms, dtype=np.complex128)
+        psi[0] = 1.0
+    gates = gates[[i for i in range(len(gates)) if gates[i]["target"] < Ms
+                   and all(c < Ms for c in gates[i]["controls"][: int(gates[i]["ncontrols"])])]]
+    orc.apply_circuit(psi, gates[:1], nthreads=nt)
+    t0 = time.perf_counter()
+    n = 1
+    while n < len(gates) and (n < min_gates + 1 or time.perf_counter() - t0 < budget_s):
+        orc.apply_circuit(psi, gates[n:n + 1], nthreads=nt)
+        n += 1
+    dt = time.perf_counter() - t0
+    return (n - 1) * float(1 << Ms) / dt, n - 1, dt, nt, Ms
+
+
+def workload_circuit(wl):
+    from workloads import generators as W
+    if wl["circuit"] == "brickwork":
+        c = W.circuit_c4_brickwork_toffoli(wl["M"], layers=24, sigma=wl["sigma"])
+        c["n_logical_gates"] = len(c["ideal"])
+        return c, None
+    c = W.circuit_c2_qft(wl["M"], sigma=wl["sigma"])
+    return c, W.random_state(wl["M"], seed=2)
+
+
+# ---------------------------------------------------------------- ours ---
+def _timed_steps(step, plans, steps, warm, stream, world, local, M):
+    """Run `warm` untimed steps, then time exactly `steps` with CUDA events on
+    the launching stream (barrier and synchronisation on both sides), with the
+    plans' per-launch timing on.  Returns (ms per step, last result, roofline,
+    launches per step, algorithmic bytes per step, launches per plan, clocks)."""
+    import torch
+    out = None
+    for _ in range(warm):
+        out = step()
+    torch.cuda.synchronize()
+    for p in plans:
+        p.set_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            out = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+    roof, launches, bytes_step, per_plan = plan_roofline(plans, ms, steps, M)
+    for p in plans:
+        p.set_timing(False)
+    return ms, out, roof, launches, bytes_step, per_plan, clk.summary()
+
+
+def run_brickwork(args, rank, world, local):
+    """The brickwork from |0...0>: one step = reset both states, the error-free
+    and the noisy circuit in place, fidelity and norm read back.  The headline
+    uses the plans made in args.mode (AUTO by default); each other form in
+    args.modes is timed the same way beside it."""
+    import ctypes
+
+    import torch
+
+    import paper_quant_ph_9804039_gb300 as qs
+
+    wl = WORKLOADS[args.workload]
+    M = wl["M"]
+    c, _ = workload_circuit(wl)
+    n = len(c["ideal"])
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    ideal = qs.State(M, device=dev, stream=stream)
+    noisy = qs.State(M, device=dev, stream=stream)
+    spec = not args.no_specialize
+    amp_step = 2.0 * n * float(1 << M)
+    mode_names = {qs.MODE_UNFUSED: "unfused", qs.MODE_TILED: "tiled", qs.MODE_FUSED: "fused"}
+
+    def make(mode):
+        t = time.perf_counter()
+        p_i = qs.Plan(M, c["ideal"], mode=mode, specialize=spec and mode != "unfused")
+        p_n = qs.Plan(M, c["noisy"], mode=mode, specialize=spec and mode != "unfused")
+        return p_i, p_n, time.perf_counter() - t
+
+    def stepper(p_i, p_n):
+        def step():
+            ideal.reset()
+            noisy.reset()
+            p_i.execute(ideal)
+            p_n.execute(noisy)
+            return qs.fidelity(ideal, noisy)
+        return step
+
+    p_i, p_n, t_plan = make(args.mode)
+    head = mode_names[p_n.stats()["mode"]]
+    auto_line = next((ln for ln in p_n.describe().splitlines() if ln.startswith("auto:")), None)
+    ms, (F, nrm), roof, launches, bytes_step, per_plan, clocks = _timed_steps(
+        stepper(p_i, p_n), [p_i, p_n], args.steps, args.warmup, stream, world, local, M)
+    value = job_throughput(amp_step, world, ms)
+    st = p_n.stats()
+    modes = {head: {"amp_updates_per_s": value, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                    "passes_per_circuit": per_plan[1], "blocks_per_circuit": st["n_blocks"],
+                    "specialised_passes": "specialised" in p_n.describe(), "plan_create_s": round(t_plan, 3),
+                    "roofline": roof, "F": F, "norm": nrm}}
     result = {
         "metric": "amplitude-updates/s", "value": value, "unit": "amp-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
-        "config": {"workload": args.workload, "M": M, "circuit": "qft", "sigma": wl["sigma"],
+        "config": {"workload": args.workload, "M": M, "circuit": "brickwork+toffoli", "layers": 24,
+                   "sigma": wl["sigma"], "gates_per_circuit": n, "circuits_per_step": 2, "input": "|0...0>",
+                   "mode": args.mode, "executed_as": head, "auto_choice": auto_line,
+                   "l2": f"inputs larger than L2 ({(8 << M) >> 20} MiB per state)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roof,
+        "fidelity": F, "norm": nrm,
+        "hbm_gbs_step": (bytes_step + 2 * 8 * float(1 << M) + 16 * float(1 << M)) / (ms / 1e3) / 1e9,
+        "clocks": clocks,
+    }
+    # launches per step: the plans' own + 2 resets + the reduction's 2 kernels
+    result["gpu_launches"] = int((launches + 4) * args.steps)
+
+    # end to end through the C ABI: host gate records in, F and the norm out.
+    # Each step resets both states, plans and applies both circuits from the
+    # host records (qsim_apply_circuit: the plan's tables are built on the
+    # host and copied to the device inside the call) and reads F back.
+    if not args.no_e2e:
+        lib = qs.load_library()
+        gi = np.ascontiguousarray(c["ideal"], dtype=qs.GATE_DTYPE)
+        gn = np.ascontiguousarray(c["noisy"], dtype=qs.GATE_DTYPE)
+        o = qs._opts("auto", 0, 0, False, False)
+        Fv, Nv = ctypes.c_double(), ctypes.c_double()
+
+        def e2e_step():
+            qs._check(lib.qsim_reset(ideal.handle))
+            qs._check(lib.qsim_reset(noisy.handle))
+            qs._check(lib.qsim_apply_circuit(ideal.handle, gi.ctypes.data_as(ctypes.c_void_p), len(gi),
+                                             ctypes.byref(o)))
+            qs._check(lib.qsim_apply_circuit(noisy.handle, gn.ctypes.data_as(ctypes.c_void_p), len(gn),
+                                             ctypes.byref(o)))
+            qs._check(lib.qsim_fidelity(ideal.handle, noisy.handle, ctypes.byref(Fv), ctypes.byref(Nv)))
+
+        ke = max(1, min(args.steps, 2))
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = max_over_ranks((time.perf_counter() - t0) / ke, world)
+        tables = qs.Plan(M, c["noisy"], mode="auto").stats()["table_bytes"] * 2
+        result["e2e"] = {"value": job_throughput(amp_step, world, dt * 1e3), "unit": "amp-updates/s",
+                         "ms_per_step": dt * 1e3, "steps": ke,
+                         "h2d_bytes_per_step": int(gi.nbytes + gn.nbytes + tables), "d2h_bytes_per_step": 24,
+                         "path": "qsim_reset x2, qsim_apply_circuit x2 from host gate records (plan built and "
+                                 "its tables copied in the call), qsim_fidelity",
+                         "F": Fv.value}
+
+    del p_i, p_n
+    for mode in [m for m in args.modes.split(",") if m and m != head]:
+        if mode == "unfused" and args.no_unfused:
+            continue
+        q_i, q_n, t_plan = make(mode)
+        steps, warm = (1, 0) if mode == "unfused" else (max(1, min(args.steps, 2)), 1)
+        msm, (Fm, nm), roofm, _, _, per_plan, clk = _timed_steps(
+            stepper(q_i, q_n), [q_i, q_n], steps, warm, stream, world, local, M)
+        modes[mode] = {"amp_updates_per_s": job_throughput(amp_step, world, msm), "ms_per_step": msm,
+                       "steps": steps, "warmup": warm, "passes_per_circuit": per_plan[1],
+                       "specialised_passes": "specialised" in q_n.describe(), "plan_create_s": round(t_plan, 3),
+                       "roofline": roofm, "F": Fm, "norm": nm, "clocks": clk}
+        del q_i, q_n
+    for m, d in modes.items():
+        d["speedup_of_unfused"] = (modes["unfused"]["ms_per_step"] / d["ms_per_step"]) if "unfused" in modes else None
+    result["modes"] = modes
+    del ideal, noisy
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return result, c, None
+
+
+def run_qft(args, world, local, workload, mode, steps, warmup):
+    """The quantum FFT: one step = the error-free and the noisy circuit, both
+    out of place from the resident input state, then the fidelity and norm."""
+    import ctypes
+
+    import torch
+
+    import paper_quant_ph_9804039_gb300 as qs
+
+    wl = WORKLOADS[workload]
+    M = wl["M"]
+    c, x = workload_circuit(wl)
+    n_logical = c["n_logical_gates"]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    xin = qs.State(M, device=dev, stream=stream, zero=False).set(x)
+    ideal = qs.State(M, device=dev, stream=stream, zero=False)
+    noisy = qs.State(M, device=dev, stream=stream, zero=False)
+    spec = not args.no_specialize
+    t_plan = time.perf_counter()
+    p_ideal = qs.Plan(M, c["ideal"], mode=mode, tile_bits=args.tile_bits, specialize=spec)
+    p_noisy = qs.Plan(M, c["noisy"], mode=mode, tile_bits=args.tile_bits, specialize=spec)
+    t_plan = time.perf_counter() - t_plan
+    specialised = "specialised" in p_noisy.describe()
+    st_n = p_noisy.stats()
+    amp_updates_step = 2.0 * n_logical * float(1 << M)
+
+    def step():
+        p_ideal.execute(ideal, xin)
+        p_noisy.execute(noisy, xin)
+        return qs.fidelity(ideal, noisy)
+
+    ms, (F, nrm), roof, launches, bytes_step, per_plan, clocks = _timed_steps(
+        step, [p_ideal, p_noisy], steps, warmup, stream, world, local, M)
+    value = job_throughput(amp_updates_step, world, ms)
+    result = {
+        "metric": "amplitude-updates/s", "value": value, "unit": "amp-updates/s", "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+        "config": {"workload": workload, "M": M, "circuit": "qft", "sigma": wl["sigma"],
                    "gates_per_circuit": n_logical, "gate_records_per_circuit": int(len(c["noisy"])),
                    "circuits_per_step": 2, "mode": mode, "tile_bits": st_n["tile_bits"],
-                   "passes_per_circuit": plan_launches[1], "specialised_passes": specialised,
+                   "passes_per_circuit": per_plan[1], "specialised_passes": specialised,
                    "plan_create_s": round(t_plan, 3),
                    "l2": f"inputs larger than L2 ({(8 << M) >> 20} MiB per state)",
                    "parallelism": f"replicas{world}"},
-        "roofline": roofline,
-        "gpu_launches": int(launches_step * args.steps),
+        "roofline": roof,
+        "gpu_launches": int((launches + 2) * steps),  # + the overlap reduction's two kernels
         "fidelity": F, "norm": nrm,
         "hbm_gbs_step": (bytes_step + 2 * 8 * float(1 << M)) / (ms / 1e3) / 1e9,
+        "clocks": clocks,
     }
-    result["clocks"] = clk.summary()
 
     # end to end through the C ABI with host buffers: every step copies its
     # input from pinned host memory and reads F and the norm back.  Pipelined
@@ -316,19 +569,18 @@ def run_ours(args, rank, world, local):
         xh = [torch.empty(1 << M, dtype=torch.complex64, pin_memory=True) for _ in range(2)]
         for h in xh:
             h.numpy()[:] = x
-        ke = max(2, min(args.steps, 10))
-        import ctypes
+        ke = max(2, min(steps, 10))
         lib = qs.load_library()
         Fv, Nv = ctypes.c_double(), ctypes.c_double()
         copy_stream = torch.cuda.Stream(device=dev)
         xq = [qs.State(M, device=dev, stream=copy_stream, zero=False) for _ in range(2)]
 
-        def e2e_run(n):
+        def e2e_run(k_steps):
             xq[0].set_async(xh[0])
-            for k in range(n):
+            for k in range(k_steps):
                 p_ideal.execute(ideal, xq[k % 2])
                 p_noisy.execute(noisy, xq[k % 2])
-                if k + 1 < n:
+                if k + 1 < k_steps:
                     xq[(k + 1) % 2].set_async(xh[(k + 1) % 2])
                 qs._check(lib.qsim_fidelity(ideal.handle, noisy.handle, ctypes.byref(Fv), ctypes.byref(Nv)))
 
@@ -344,42 +596,51 @@ def run_ours(args, rank, world, local):
                          "ms_per_step": dt * 1e3, "h2d_bytes_per_step": int(x.nbytes),
                          "d2h_bytes_per_step": 24, "steps": ke,
                          "pipelined": "input copy of step k+1 overlaps the passes of step k (two input states)"}
-        del xq
+        del xq, xh
 
     # one-gate-per-launch form on the same GPU
     if not args.no_unfused and mode != "unfused":
         pu_i = qs.Plan(M, c["ideal"], mode="unfused")
         pu_n = qs.Plan(M, c["noisy"], mode="unfused")
-        ku = max(1, min(args.steps, 3))
-        pu_i.execute(ideal, xin)
-        pu_n.execute(noisy, xin)
-        qs.fidelity(ideal, noisy)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(ku):
+
+        def ustep():
             pu_i.execute(ideal, xin)
             pu_n.execute(noisy, xin)
-            Fu, _ = qs.fidelity(ideal, noisy)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msu = max_over_ranks(e0.elapsed_time(e1) / ku, world)
-        result["unfused"] = {"value": job_throughput(amp_updates_step, world, msu), "ms_per_step": msu,
-                             "launches_per_step": pu_i.stats()["n_launches"] + pu_n.stats()["n_launches"] + 2,
-                             "fidelity": Fu, "speedup_of_value": msu / ms}
-        del pu_i, pu_n
+            return qs.fidelity(ideal, noisy)
 
+        ku = max(1, min(steps, 3))
+        msu, (Fu, _), _, lu, _, _, _ = _timed_steps(ustep, [pu_i, pu_n], ku, 1, stream, world, local, M)
+        result["unfused"] = {"value": job_throughput(amp_updates_step, world, msu), "ms_per_step": msu,
+                             "launches_per_step": lu + 2, "fidelity": Fu, "speedup_of_value": msu / ms}
+        del pu_i, pu_n
+    del xin, ideal, noisy, p_ideal, p_noisy
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return result, c, x
+
+
+def run_ours(args, rank, world, local):
+    wl = WORKLOADS[args.workload]
+    if wl["circuit"] == "brickwork":
+        result, c, x = run_brickwork(args, rank, world, local)
+        if not args.no_qft:
+            q, _, _ = run_qft(args, world, local, "qft-m28-c64", "tiled", 20, 3)
+            result["qft_m28"] = {k: q[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "config",
+                                                   "roofline", "e2e", "unfused", "fidelity", "norm", "clocks",
+                                                   "gpu_launches", "hbm_gbs_step") if k in q}
+    else:
+        result, c, x = run_qft(args, world, local, args.workload, args.mode, args.steps, args.warmup)
     if not args.no_extras:
-        del xin, ideal, noisy, p_ideal, p_noisy
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
+        import torch
+        stream = torch.cuda.current_stream()
         result["single_gate"] = bench_single_gate(stream)
-        result["batched"] = bench_trajectories(world)
+        result["batched"] = bench_trajectories(world, result["clocks"].get("sm_mhz"))
         result["serving"] = bench_serving(args.serve_requests, world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, ng, dt, nt = oracle_sample(M, c["noisy"], x, budget_s=15.0)
+        v, ng, dt, nt, Ms = oracle_sample(wl["M"], c["noisy"], x, budget_s=15.0)
         result["cpu_baseline"] = {"value": v, "unit": "amp-updates/s", "cores": nt, "kind": "oracle",
-                                  "sample": f"first {ng} gates of the noisy circuit at M={M} "
+                                  "sample": f"first {ng} gates of the noisy circuit at M={Ms} "
                                             f"(complex128), {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -423,10 +684,17 @@ def bench_single_gate(stream):
     return out
 
 
-def bench_trajectories(world):
+def bench_trajectories(world, sm_mhz=None):
     """Batched error trajectories: M=16, T=4096, 20-layer brickwork, sigma=5e-3,
     one persistent launch replayed from a CUDA graph; against running the
-    same trajectories one circuit at a time, one gate per launch."""
+    same trajectories one circuit at a time, one gate per launch (their
+    plans made before the timed loop).
+
+    Roofline (ALU-bound: every trajectory lives on chip): algorithmic flops
+    = 16 per amplitude per dense 2x2 complex gate (8 FMA: two complex
+    products and a sum per output), 0 for the CNOTs (a permutation), against
+    the FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flop x the SM
+    clock sampled during the timed region."""
     import paper_quant_ph_9804039_gb300 as qs
     from workloads import generators as W
     M, T = 16, 4096
@@ -439,34 +707,48 @@ def bench_trajectories(world):
     for _ in range(reps):
         F, mean, var = plan.run(eps)
     dt = (time.perf_counter() - t0) / reps
+    n_dense = int(sum(1 for r in b["ideal"] if int(r["ncontrols"]) == 0))
+    flops = T * n_dense * 16.0 * float(1 << M)
+    mhz = sm_mhz or 2070.0
+    peak = derived_fp32_peak(mhz)
     # sequential one-gate-per-launch form on a sample of trajectories
     ideal = qs.State(M)
     qs.Plan(M, b["ideal"], mode="unfused").execute(ideal)
     noisy = qs.State(M)
     ns = 16
+    plans = [qs.Plan(M, W.with_errors(b["ideal"], b["axes"], eps[t]), mode="unfused") for t in range(ns)]
+    plans[0].execute(noisy)
+    qs.fidelity(ideal, noisy)
     t0 = time.perf_counter()
     for t in range(ns):
-        rec = W.with_errors(b["ideal"], b["axes"], eps[t])
         noisy.reset()
-        qs.Plan(M, rec, mode="unfused").execute(noisy)
+        plans[t].execute(noisy)
         qs.fidelity(ideal, noisy)
     dts = (time.perf_counter() - t0) / ns
     info = plan.info()
     return {"workload": "brickwork-m16-t4096", "trajectories_per_s": world * T / dt, "s_per_batch": dt,
             "mean_F": mean, "var_F": var, "tile_bits": info["tile_bits"], "passes": info["n_passes"],
-            "grid": info["grid"], "gates": int(len(b["ideal"])),
+            "grid": info["grid"], "gates": int(len(b["ideal"])), "dense_gates": n_dense,
             "amp_updates_per_s": world * T * len(b["ideal"]) * float(1 << M) / dt,
+            "roofline": {"bound": "alu", "achieved": flops / dt, "peak": peak, "unit": "FLOP/s",
+                         "frac": round(flops / dt / peak, 4),
+                         "peak_source": f"derived: {GB300_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                        f"{mhz:.0f} MHz" + (" (sampled)" if sm_mhz else " (maximum clock)"),
+                         "flops": "16 per amplitude per dense complex 2x2 gate, 0 per CNOT"},
             "sequential_unfused_trajectories_per_s": 1.0 / dts,
-            "sequential_sample": f"{ns} trajectories, errors applied on the host, one gate per launch"}
+            "sequential_sample": f"{ns} trajectories, one gate per launch, plans made before the timed loop",
+            "speedup_of_sequential": (T / dt) * dts}
 
 
 def bench_serving(n_requests, world):
     """Served stream: Poisson arrivals, M ~ U{12..26}, 50..500 gates, sigma
-    log-uniform in [1e-5, 1e-2], 160 GiB budget.  The offered rate is the
-    measured capacity of the sequential one-gate-per-launch loop (load 1.0
-    for it).  Latency = completion - arrival.  The sequential loop serves a
-    sample of the same stream live (one request at a time, in arrival order);
-    the continuous-batching server serves the whole stream."""
+    log-uniform in [1e-5, 1e-2], 160 GiB budget.  The base offered rate is
+    the measured capacity of the sequential one-gate-per-launch loop (load
+    1.0 for it).  Latency = completion - arrival.  The sequential loop serves
+    a sample of the stream live (one request at a time, in arrival order);
+    the continuous-batching server serves the whole stream at the base rate,
+    then again at 4x and 16x the base rate to find its saturation
+    throughput, and once with every request submitted at t = 0."""
     import paper_quant_ph_9804039_gb300 as qs
     from workloads import generators as W
     reqs = W.serving_requests(n_requests)
@@ -498,66 +780,87 @@ def bench_serving(n_requests, world):
         serve_one(r, c)
         seq_lat.append(time.perf_counter() - t_start - t_arr)
     seq_rate = ns / (time.perf_counter() - t_start)
-    # the continuous-batching server under the whole stream
-    srv = qs.Server(hbm_budget=160 << 30, max_slots=16, mode="tiled")
-    t_start = time.perf_counter()
-    t_arr = 0.0
-    arrival = {}
-    done = []
-    for r, c in zip(reqs, circs):
-        t_arr += r["gap"] / lam
-        while time.perf_counter() - t_start < t_arr:
-            done += srv.poll(256, wait_ms=0)
-            time.sleep(0.0002)
-        rid = srv.submit(r["M"], c["ideal"], c["noisy"])
-        arrival[rid] = time.perf_counter()
-    while len(done) < len(reqs):
-        done += srv.poll(256, wait_ms=100)
-    t_end = time.perf_counter()
-    st = srv.stats()
-    srv.close()
-    lat = np.array([d["t_done"] - d["t_submit"] for d in done])
-    ok = sum(1 for d in done if d["status"] == 0)
-    return {"workload": "served-stream", "requests": len(reqs), "ok": ok, "offered_rate": lam,
-            "requests_per_s": world * len(reqs) / (t_end - t_start),
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "max_active": st["max_active"], "peak_state_bytes": st["peak_bytes"],
-            "sequential_unfused": {"requests_per_s": seq_rate, "sample": ns,
-                                   "p50_ms": float(np.percentile(seq_lat, 50) * 1e3),
-                                   "p99_ms": float(np.percentile(seq_lat, 99) * 1e3)}}
+
+    def serve_stream(rate, sel):
+        """The server under the requests `sel` arriving at `rate` (None: all at once)."""
+        srv = qs.Server(hbm_budget=160 << 30, max_slots=16, mode="tiled")
+        t_start = time.perf_counter()
+        t_arr = 0.0
+        done = []
+        for r, c in sel:
+            if rate is not None:
+                t_arr += r["gap"] / rate
+                while time.perf_counter() - t_start < t_arr:
+                    done += srv.poll(256, wait_ms=0)
+                    time.sleep(0.0002)
+            srv.submit(r["M"], c["ideal"], c["noisy"])
+        while len(done) < len(sel):
+            done += srv.poll(256, wait_ms=100)
+        t_end = time.perf_counter()
+        st = srv.stats()
+        srv.close()
+        lat = np.array([d["t_done"] - d["t_submit"] for d in done])
+        return {"offered_rate": rate, "requests": len(sel), "ok": sum(1 for d in done if d["status"] == 0),
+                "requests_per_s": world * len(sel) / (t_end - t_start),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "max_active": st["max_active"], "peak_state_bytes": st["peak_bytes"]}
+
+    pairs = list(zip(reqs, circs))
+    base = serve_stream(lam, pairs)
+    loads = {}
+    for mult in (4, 16):
+        loads[f"{mult}x"] = serve_stream(lam * mult, pairs)
+    loads["all_at_t0"] = serve_stream(None, pairs)
+    sat = max(v["requests_per_s"] for v in loads.values())
+    out = {"workload": "served-stream", "requests": len(reqs), "ok": base["ok"], "offered_rate": lam,
+           "requests_per_s": base["requests_per_s"], "p50_ms": base["p50_ms"], "p99_ms": base["p99_ms"],
+           "max_active": base["max_active"], "peak_state_bytes": base["peak_state_bytes"],
+           "higher_loads": loads, "saturation_requests_per_s": sat,
+           "sequential_unfused": {"requests_per_s": seq_rate, "capacity_requests_per_s": lam, "sample": ns,
+                                  "p50_ms": float(np.percentile(seq_lat, 50) * 1e3),
+                                  "p99_ms": float(np.percentile(seq_lat, 99) * 1e3)},
+           "saturation_over_sequential_capacity": sat / lam}
+    return out
 
 
 # ---------------------------------------------------------- reference arm ---
 def run_reference(args, rank, world):
     """The CPU oracle as it stands, on the host cores, same metric and config;
-    each step is a bounded sample (the first gates of the noisy circuit)."""
+    each step is a bounded sample (consecutive gates of the noisy circuit, at
+    the workload's M when the host has the memory)."""
     if rank != 0:
         return
-    from workloads import generators as W
     import oracle
 
     wl = WORKLOADS[args.workload]
-    M = wl["M"]
-    c = W.circuit_c2_qft(M, sigma=wl["sigma"])
-    x = W.random_state(M, seed=2)
+    c, x = workload_circuit(wl)
+    M = oracle_size(wl["M"])
+    gates = c["noisy"]
+    gates = gates[[i for i in range(len(gates)) if gates[i]["target"] < M
+                   and all(q < M for q in gates[i]["controls"][: int(gates[i]["ncontrols"])])]]
     orc = oracle.Oracle()
     nt = oracle.default_threads()
-    psi = x.astype(np.complex128)
+    if x is not None and M == wl["M"]:
+        psi = x.astype(np.complex128)
+    else:
+        psi = np.zeros(1 << M, dtype=np.complex128)
+        psi[0] = 1.0
+    orc.apply_circuit(psi, gates[:1], nthreads=nt)  # touches every page
     t0 = time.perf_counter()
-    orc.apply_circuit(psi, c["noisy"][:1], nthreads=nt)
+    orc.apply_circuit(psi, gates[1:2], nthreads=nt)
     t1 = time.perf_counter() - t0
     total_steps = args.steps + args.warmup
     per_step = max(1, int(min(8.0, 150.0 / max(1, total_steps)) / max(t1, 1e-6)))
-    g = 1
+    g = 2
     for _ in range(args.warmup):
-        orc.apply_circuit(psi, c["noisy"][g:g + per_step], nthreads=nt)
-        g = (g + per_step) % len(c["noisy"])
+        orc.apply_circuit(psi, gates[g:g + per_step], nthreads=nt)
+        g = (g + per_step) % len(gates)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        sel = c["noisy"][g:g + per_step]
+        sel = gates[g:g + per_step]
         if len(sel) < per_step:
             g = 0
-            sel = c["noisy"][:per_step]
+            sel = gates[:per_step]
         orc.apply_circuit(psi, sel, nthreads=nt)
         g += per_step
     dt = (time.perf_counter() - t0) / args.steps
@@ -568,91 +871,11 @@ def run_reference(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "complex128",
         "data": "synthetic",
-        "config": {"workload": args.workload, "M": M, "circuit": "qft", "sigma": wl["sigma"]},
+        "config": {"workload": args.workload, "M": wl["M"], "circuit": wl["circuit"], "sigma": wl["sigma"],
+                   "oracle_M": M},
         "cpu_baseline": {"value": v, "unit": "amp-updates/s", "cores": nt, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "amp-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
-
-
-def run_brickwork(args, rank, world, local):
-    """The M=33 brickwork from |0...0>: per mode, one step = reset both states,
-    the error-free and the noisy circuit in place, fidelity and norm read back."""
-    import torch
-
-    import paper_quant_ph_9804039_gb300 as qs
-    from workloads import generators as W
-
-    wl = WORKLOADS[args.workload]
-    M = wl["M"]
-    c = W.circuit_c4_brickwork_toffoli(M, layers=24, sigma=wl["sigma"])
-    n = len(c["ideal"])
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.set_stream(stream)
-    ideal = qs.State(M, device=dev, stream=stream)
-    noisy = qs.State(M, device=dev, stream=stream)
-    peak, peak_src = measured_peaks()
-    modes = {}
-    # a step here takes seconds: at most 5 timed steps per mode
-    k = max(1, min(args.steps, 5))
-    for mode, steps, warm in (("tiled", k, max(1, min(args.warmup, 2))),
-                              ("fused", k, max(1, min(args.warmup, 2))),
-                              ("unfused", 1, 0)):
-        if mode == "unfused" and args.no_unfused:
-            continue
-        spec = mode == "tiled" and not args.no_specialize
-        p_i = qs.Plan(M, c["ideal"], mode=mode, specialize=spec)
-        p_n = qs.Plan(M, c["noisy"], mode=mode, specialize=spec)
-
-        def step():
-            ideal.reset()
-            noisy.reset()
-            p_i.execute(ideal)
-            p_n.execute(noisy)
-            return qs.fidelity(ideal, noisy)
-
-        for _ in range(warm):
-            step()
-        torch.cuda.synchronize()
-        p_i.set_timing(True)
-        p_n.set_timing(True)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        barrier(world)
-        with ClockSampler(local) as clk:
-            e0.record(stream)
-            for _ in range(steps):
-                F, nrm = step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
-        tot_ms = tot_bytes = 0.0
-        for p in (p_i, p_n):
-            t_ms, t_bytes, _, execs = p.timing()
-            tot_ms += sum(t_ms)
-            tot_bytes += sum(t_bytes) * execs
-        st = p_n.stats()
-        gbs = tot_bytes / (tot_ms / 1e3) / 1e9
-        modes[mode] = {"amp_updates_per_s": job_throughput(2.0 * n * float(1 << M), world, ms), "ms_per_step": ms,
-                       "specialised_passes": "specialised" in p_n.describe(),
-                       "steps": steps, "warmup": warm, "passes_per_circuit": st["n_passes"],
-                       "launch_GB/s": round(gbs, 1), "launch_frac_of_measured_hbm": round(gbs / peak, 4),
-                       "F": F, "norm": nrm, "clocks": clk.summary()}
-        p_i.set_timing(False)
-        p_n.set_timing(False)
-        del p_i, p_n
-    best = max(modes, key=lambda m: modes[m]["amp_updates_per_s"])
-    if rank == 0:
-        print(json.dumps({
-            "metric": "amplitude-updates/s", "value": modes[best]["amp_updates_per_s"], "unit": "amp-updates/s",
-            "n_gpus": world, "steps": modes[best]["steps"], "warmup": modes[best]["warmup"],
-            "ms_per_step": modes[best]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
-            "config": {"workload": args.workload, "M": M, "circuit": "brickwork+toffoli", "layers": 24,
-                       "sigma": wl["sigma"], "gates_per_circuit": n, "circuits_per_step": 2, "input": "|0...0>",
-                       "best_mode": best, "l2": "inputs larger than L2 (64 GiB per state)",
-                       "parallelism": f"replicas{world}"},
-            "modes": modes, "peak_GB/s": peak, "peak_source": peak_src}), flush=True)
 
 
 def main():
@@ -662,10 +885,7 @@ def main():
         run_reference(args, rank, world)
         return
     dist_init(world, local)
-    if args.workload.startswith("brickwork"):
-        run_brickwork(args, rank, world, local)
-    else:
-        run_ours(args, rank, world, local)
+    run_ours(args, rank, world, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -93,6 +93,11 @@ typedef struct qsim_opts {
                          * masks and matrix entries as constants) and compiled with NVRTC at plan
                          * creation: slower creation (about a second), faster execution, same
                          * results; without NVRTC the plan keeps the general kernel */
+    int32_t wait_us;    /* QSIM_MODE_FUSED: bound of the tensor-core kernel's pipeline waits, in
+                         * microseconds; 0 = 2 s.  A wait that runs out stops the kernel (the CTA
+                         * drains its copies and MMAs in flight, with the full 2 s bound, and
+                         * frees its tensor memory) and qsim_plan_status then reports
+                         * QSIM_ETIMEOUT; the state is undefined.  For failure-detection tests */
 } qsim_opts;
 
 /* Counts describing one execution of a plan. */
@@ -108,6 +113,8 @@ typedef struct qsim_plan_stats {
     int32_t n_blocks;      /* fused blocks (QSIM_MODE_FUSED) */
     double algo_bytes;     /* algorithmic device-memory bytes (read + write) per execution */
     double amp_updates;    /* n_gates * 2^M */
+    int64_t table_bytes;   /* device bytes of the plan's tables (gate ops, rounds, phase runs, fused
+                            * matrices), copied from the host when the plan is created */
 } qsim_plan_stats;
 
 typedef struct qsim_state qsim_state;   /* opaque; owned by the library */
@@ -246,21 +253,23 @@ int qsim_probabilities(const qsim_state *st, void *out, int on_device);
 
 /* Fidelity and norm for callers that cannot allocate device memory.  The
  * paper has no counterpart: this entry point exists for code that must not
- * call cudaMalloc -- work being captured into a CUDA graph, plugins whose host
- * application owns all GPU memory through its own pool, latency-critical
- * loops -- and so cannot create the qsim_state that qsim_fidelity needs.
+ * call cudaMalloc -- plugins whose host application owns all GPU memory
+ * through its own pool, latency-critical loops that must never enter the
+ * allocator -- and so cannot create the qsim_state that qsim_fidelity needs.
  *
  * ideal_amps, noisy_amps: caller-owned device arrays of 2^M amplitudes
  * (16-byte aligned; ideal_amps may be NULL for the norm alone, F is then 0).
  * Computes the same F = |sum conj(ideal_i) noisy_i|^2 and norm_noisy =
  * sum |noisy_i|^2 as qsim_fidelity, on cuda_stream (NULL = legacy default),
- * and waits for it.  Allocates nothing: its scratch is one fixed 1.5 MiB
- * device array that every GPU which loads the library holds until the
- * process exits, so M is limited to [1, 32]; larger M returns QSIM_EINVAL
- * with a message.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
- * calls share the array and it keeps the last call's values; calls whose
- * work overlaps on the GPU (other streams or host threads) race on it. */
+ * then copies the result to the host and waits for that stream.  Allocates
+ * nothing: its scratch is one fixed 1.5 MiB device array that every GPU which
+ * loads the library holds until the process exits, so M is limited to
+ * [1, 32]; larger M returns QSIM_EINVAL with a message.  The first call on a
+ * device looks the array's address up (cudaGetSymbolAddress) and keeps it for
+ * the life of the process (a cudaDeviceReset in between is not supported);
+ * that first call should come before any stream capture.  All calls share
+ * the array and it keeps the last call's values; calls whose work overlaps
+ * on the GPU (other streams or host threads) race on it. */
 int qsim_fidelity_noalloc(const void *ideal_amps, const void *noisy_amps, int M, qsim_prec prec,
                           void *cuda_stream, double *F, double *norm_noisy);
 
@@ -370,6 +379,37 @@ int qsim_server_get_stats(qsim_server *srv, qsim_server_stats *out);
 /* Finish every queued request, then stop and release everything.  Results
  * not polled are dropped. */
 void qsim_server_destroy(qsim_server *srv);
+
+/* ------------------------------------------------------ device memory */
+
+/* Device-memory hook (outside the paper; a deployment matter: the library's
+ * state vectors and tables can then live in the caller's memory pool, e.g.
+ * a framework's caching allocator, instead of next to it).
+ *
+ * alloc(bytes, cuda_stream, ctx) returns `bytes` of device memory on the
+ * current device, 256-byte aligned, or NULL when it has none (the library
+ * call then fails with QSIM_ENOMEM).  cuda_stream is the stream on which the
+ * library first uses the memory (NULL = legacy default stream); a
+ * stream-ordered allocator may hand out memory whose earlier users are
+ * ordered before that stream's later work.  free(ptr, bytes, cuda_stream,
+ * ctx) gives it back: the library's work on ptr is queued on cuda_stream (or
+ * already complete) when free is called.
+ *
+ * Every device allocation the library makes after this call goes through the
+ * pair: qsim_alloc's amplitudes and every state's reduction scratch, plan
+ * tables, trajectory-plan workspaces, and the server's state vectors and
+ * scratch (the server then leaves its own memory pool unused; its HBM budget
+ * still counts the bytes).  Each state, plan, trajectory plan and server
+ * keeps the pair it was created with and releases its memory through it, so
+ * the functions and ctx must stay valid until every object created under
+ * them is released.  Not routed: pinned host staging buffers, and the module
+ * memory of kernels compiled at plan creation (NVRTC), which the CUDA driver
+ * allocates.  alloc = free = NULL restores the CUDA runtime (cudaMalloc /
+ * cudaMallocAsync).  QSIM_EINVAL if exactly one of the two is NULL.  The
+ * hook may be called from the server's scheduler thread. */
+typedef void *(*qsim_device_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx);
+typedef void (*qsim_device_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *ctx);
+int qsim_set_allocator(qsim_device_alloc_fn alloc, qsim_device_free_fn free, void *ctx);
 
 /* ---------------------------------------------------------------- misc */
 

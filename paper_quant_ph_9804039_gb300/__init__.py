@@ -44,13 +44,14 @@ class QsimError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("fuse_k", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32), ("wait_us", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
     _fields_ = [("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_launches", ctypes.c_int64),
                 ("mode", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("fuse_k", ctypes.c_int32),
-                ("n_blocks", ctypes.c_int32), ("algo_bytes", ctypes.c_double), ("amp_updates", ctypes.c_double)]
+                ("n_blocks", ctypes.c_int32), ("algo_bytes", ctypes.c_double), ("amp_updates", ctypes.c_double),
+                ("table_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -130,6 +131,7 @@ SIGNATURES = [
     ("qsim_server_poll", ctypes.c_int, [_vp, ctypes.POINTER(RequestResult), ctypes.c_int, _ip, ctypes.c_int]),
     ("qsim_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
     ("qsim_server_destroy", None, [_vp]),
+    ("qsim_set_allocator", ctypes.c_int, [_vp, _vp, _vp]),
     ("qsim_last_error", ctypes.c_char_p, []),
     ("qsim_version", ctypes.c_char_p, []),
 ]
@@ -175,9 +177,9 @@ def _records(gates) -> np.ndarray:
     return np.ascontiguousarray(gates, dtype=GATE_DTYPE)
 
 
-def _opts(mode="auto", fuse_k=0, tile_bits=0, use_graph=False, specialize=False) -> Opts:
+def _opts(mode="auto", fuse_k=0, tile_bits=0, use_graph=False, specialize=False, wait_us=0) -> Opts:
     m = _MODES[mode] if isinstance(mode, str) else int(mode)
-    return Opts(m, int(fuse_k), int(tile_bits), int(bool(use_graph)), int(bool(specialize)))
+    return Opts(m, int(fuse_k), int(tile_bits), int(bool(use_graph)), int(bool(specialize)), int(wait_us))
 
 
 def _torch():
@@ -304,13 +306,13 @@ class Plan:
     """A compiled circuit for states of M qubits (qsim_plan_create)."""
 
     def __init__(self, M: int, gates, prec="c64", mode="auto", fuse_k=0, tile_bits=0, use_graph=False,
-                 specialize=False):
+                 specialize=False, wait_us=0):
         lib = load_library()
         self.M = int(M)
         self.prec = _prec(prec)
         g = _records(gates)
         self.n_gates = len(g)
-        o = _opts(mode, fuse_k, tile_bits, use_graph, specialize)
+        o = _opts(mode, fuse_k, tile_bits, use_graph, specialize, wait_us)
         h = _vp()
         _check(lib.qsim_plan_create(self.M, self.prec, _vp(g.ctypes.data), len(g), ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -462,3 +464,49 @@ def run_trajectories(M: int, gates, err_axis, eps, fuse_k: int = 0, use_graph: b
 
 def version() -> str:
     return load_library().qsim_version().decode()
+
+
+# qsim_device_alloc_fn / qsim_device_free_fn of include/qsim.h
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = None  # the registered callbacks, kept alive while the library may call them
+
+
+def set_allocator(alloc=None, free=None):
+    """qsim_set_allocator with Python callables: alloc(bytes, stream) -> device
+    address (int, 0 on failure) and free(ptr, bytes, stream); None, None
+    restores the CUDA runtime.  Objects created under a pair keep calling it
+    until they are released, so the callables are kept alive here."""
+    global _hooks
+    lib = load_library()
+    if alloc is None and free is None:
+        _check(lib.qsim_set_allocator(None, None, None))
+        return
+
+    def _a(nbytes, stream, ctx):
+        try:
+            return int(alloc(int(nbytes), int(stream or 0))) or None
+        except Exception:  # reported to the library as an allocation failure
+            return None
+
+    def _f(ptr, nbytes, stream, ctx):
+        free(int(ptr), int(nbytes), int(stream or 0))
+
+    ca, cf = ALLOC_FN(_a), FREE_FN(_f)
+    _check(lib.qsim_set_allocator(ctypes.cast(ca, _vp), ctypes.cast(cf, _vp), None))
+    _hooks = (_hooks or ()) + ((ca, cf),)  # earlier pairs stay alive for the objects made under them
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching
+    allocator (torch.cuda.caching_allocator_alloc / _delete), so that its
+    states, plan tables and workspaces share torch's memory pool."""
+    torch = _torch()
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    set_allocator(alloc, free)

@@ -92,7 +92,9 @@ static int state_common(int M, qsim_prec prec, qsim_state **out) {
 
 static int state_scratch(qsim_state *st) {
     st->scratch_blocks = kReduceSlots;
-    QS_CUDA(cudaMalloc(&st->scratch, (3 * size_t(kReduceSlots) + 4) * sizeof(double)));
+    if (int rc = dmalloc(st->alloc, reinterpret_cast<void **>(&st->scratch), state_scratch_bytes(kReduceSlots),
+                         nullptr, "reduction scratch"))
+        return rc;
     QS_CUDA(cudaEventCreateWithFlags(&st->ev, cudaEventDisableTiming));
     return QSIM_OK;
 }
@@ -111,9 +113,8 @@ int qsim_alloc(int M, qsim_prec prec, qsim_state **out) {
     st->prec = prec;
     st->owned = true;
     st->stream = nullptr;
-    cudaError_t e = cudaMalloc(&st->amps, (size_t(1) << M) * amp_bytes(prec));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
+    st->alloc = current_allocator();
+    if (dmalloc(st->alloc, &st->amps, (size_t(1) << M) * amp_bytes(prec), nullptr, "state amplitudes")) {
         delete st;
         set_error("cannot allocate %zu bytes for a %d-qubit state", (size_t(1) << M) * amp_bytes(prec), M);
         return QSIM_ENOMEM;
@@ -139,6 +140,7 @@ int qsim_wrap(void *device_amps, int M, qsim_prec prec, qsim_state **out) {
     st->owned = false;
     st->amps = device_amps;
     st->stream = nullptr;
+    st->alloc = current_allocator();
     if ((rc = state_scratch(st)) != QSIM_OK) {
         qsim_free(st);
         return rc;
@@ -150,8 +152,8 @@ int qsim_wrap(void *device_amps, int M, qsim_prec prec, qsim_state **out) {
 void qsim_free(qsim_state *st) {
     if (!st) return;
     cudaStreamSynchronize(st->stream);
-    if (st->owned && st->amps) cudaFree(st->amps);
-    if (st->scratch) cudaFree(st->scratch);
+    if (st->owned) dfree(st->alloc, st->amps, (size_t(1) << st->M) * amp_bytes(st->prec), nullptr);
+    dfree(st->alloc, st->scratch, state_scratch_bytes(st->scratch_blocks), nullptr);
     if (st->ev) cudaEventDestroy(st->ev);
     delete st;
 }
@@ -269,15 +271,15 @@ int qsim_probabilities(const qsim_state *st, void *out, int on_device) {
     const size_t pb = st->prec == QSIM_C64 ? sizeof(float) : sizeof(double);
     if (on_device) return launch_probabilities(st->amps, st->M, st->prec, out, st->stream);
     void *tmp = nullptr;
-    QS_CUDA(cudaMallocAsync(&tmp, n * pb, st->stream));
+    if (int rc = dmalloc(st->alloc, &tmp, n * pb, st->stream, "probabilities")) return rc;
     int rc = launch_probabilities(st->amps, st->M, st->prec, tmp, st->stream);
     if (rc == QSIM_OK) {
         cudaError_t e = cudaMemcpyAsync(out, tmp, n * pb, cudaMemcpyDeviceToHost, st->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "probabilities copy");
     }
-    cudaFreeAsync(tmp, st->stream);
     cudaStreamSynchronize(st->stream);
+    dfree(st->alloc, tmp, n * pb, st->stream);
     return rc;
 }
 

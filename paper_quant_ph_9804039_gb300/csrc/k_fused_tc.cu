@@ -57,10 +57,12 @@
 //                staging tile that the four warps copy out in coalesced runs.
 // The split warps release an input stage as soon as the tile is in their
 // registers, before converting it.
-// Every mbarrier wait is bounded (2 s of globaltimer); on a timeout the CTA
-// records QSIM_ETIMEOUT in the status word, the other roles leave their loops,
-// the producer waits (bounded) for its copies in flight, the MMA warp for its
-// last commit, and the CTA frees its TMEM and returns.
+// Every mbarrier wait is bounded: the main loops' waits by wait_ns (2 s by
+// default, qsim_opts.wait_us), the drain waits at the end always by 2 s of
+// globaltimer.  On a timeout the CTA records QSIM_ETIMEOUT in the status
+// word, the other roles leave their loops, the producer waits for its copies
+// in flight (cp.async.wait_all, and the R image's bulk copy), the MMA warp for
+// both commits of its last tile, and the CTA frees its TMEM and returns.
 #include <cuda_fp16.h>
 
 #include "cx.cuh"
@@ -112,21 +114,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait on an mbarrier phase; false once kWaitNs have passed or the
-// CTA is aborting.
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+// Bounded wait on an mbarrier phase of the main loops; false once limit_ns
+// have passed or the CTA is aborting.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, const volatile int *abort, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort) return false;
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
     return true;
 }
 // The same wait by every lane of a warp, with one outcome for all of them
 // (the warp stays converged for the .sync.aligned tcgen05 instructions).
-__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, const volatile int *abort) {
-    return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort)) != 0;
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, const volatile int *abort,
+                                          uint64_t limit_ns) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort, limit_ns)) != 0;
+}
+// Drain wait at the end of a CTA (copies or MMAs still in flight): always the
+// full kWaitNs, whatever the main loops' limit, and not cut short by abort.
+__device__ __forceinline__ void drain_wait(uint64_t *bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer() - t0 > kWaitNs) break;
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -258,7 +268,7 @@ __device__ __forceinline__ uint32_t stg_swz(uint32_t u, int r) { return u ^ ((u 
 template <int KF, bool DIRECT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_tc(float2 *dst, const float2 *src, FusedDesc d, const __half *__restrict__ rimg, uint64_t ntiles,
-               int *status) {
+               int *status, uint64_t wait_ns) {
     using C = Cfg<KF, DIRECT>;
     constexpr int kNIn = C::NIN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -340,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t rmask = run_amps - 1;
         for (uint64_t i = 0; i < n_local; ++i) {
             const int s = int(i % kNIn);
-            if (i >= kNIn && !warp_wait(&ctl.empty_in[s], uint32_t(((i / kNIn) & 1) ^ 1), abort)) {
+            if (i >= kNIn && !warp_wait(&ctl.empty_in[s], uint32_t(((i / kNIn) & 1) ^ 1), abort, wait_ns)) {
                 ok = false;
                 break;
             }
@@ -359,26 +369,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) atomicExch(status, QSIM_ETIMEOUT);
             ctl.abort = 1;
         }
-        if (warp == 0 && lane == 0) {
-            const uint64_t t0 = globaltimer();
-            while (!mbar_try_wait(&ctl.bar_r, 0))
-                if (globaltimer() - t0 > kWaitNs) break;
-        }
+        if (warp == 0 && lane == 0) drain_wait(&ctl.bar_r, 0);  // the R image's bulk copy has landed
         (void)issued;
         __syncwarp();
     } else if (warp == kMmaWarp) {
         // ----------------------------------------------------------------- MMA
         uint64_t done = 0;  // tiles whose MMAs were issued
         if (lane == 0) {
-            ok = mbar_wait(&ctl.bar_r, 0, abort);
+            ok = mbar_wait(&ctl.bar_r, 0, abort, wait_ns);
             const uint32_t bh = smem_u32(sm + C::OFF_B);
             const uint32_t bl = bh + (C::B_BYTES < 1024 ? 1024 : C::B_BYTES);
             constexpr uint32_t IDESC = idesc_f16(128, C::KR);
             for (uint64_t i = 0; ok && i < n_local; ++i) {
                 const int t = int(i % kNA);
                 const uint32_t ph = uint32_t((i / kNA) & 1);
-                if (!mbar_wait(&ctl.full_a[t], ph, abort)) { ok = false; break; }
-                if (i >= kNA && !mbar_wait(&ctl.empty_acc[t], ph ^ 1, abort)) { ok = false; break; }
+                if (!mbar_wait(&ctl.full_a[t], ph, abort, wait_ns)) { ok = false; break; }
+                if (i >= kNA && !mbar_wait(&ctl.empty_acc[t], ph ^ 1, abort, wait_ns)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t ah = smem_u32(sm + C::OFF_A + uint32_t(t) * 2 * kABytes);
                 const uint32_t al = ah + kABytes;
@@ -404,11 +410,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 atomicExch(status, QSIM_ETIMEOUT);
                 ctl.abort = 1;
             }
-            if (done > 0) {  // the last MMAs must be complete before TMEM is freed
+            if (done > 0) {  // the last MMAs and both their commits must be complete before TMEM is freed
                 const uint64_t j = done - 1;
-                const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(&ctl.empty_a[j % kNA], uint32_t((j / kNA) & 1)))
-                    if (globaltimer() - t0 > kWaitNs) break;
+                drain_wait(&ctl.empty_a[j % kNA], uint32_t((j / kNA) & 1));
+                drain_wait(&ctl.full_acc[j % kNA], uint32_t((j / kNA) & 1));
             }
         }
         __syncwarp();
@@ -423,9 +428,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (uint64_t i = 0; i < n_local; ++i) {
             const int s_in = int(i % kNIn), t = int(i % kNA);
             const uint32_t ph = uint32_t((i / kNA) & 1);
-            ok = warp_wait(&ctl.full_in[s_in], uint32_t((i / kNIn) & 1), abort);
-            if (ok && i >= kNA) ok = warp_wait(&ctl.empty_a[t], ph ^ 1, abort);
-            if (ok && i >= kNA) ok = warp_wait(&ctl.empty_acc[t], ph ^ 1, abort);
+            ok = warp_wait(&ctl.full_in[s_in], uint32_t((i / kNIn) & 1), abort, wait_ns);
+            if (ok && i >= kNA) ok = warp_wait(&ctl.empty_a[t], ph ^ 1, abort, wait_ns);
+            if (ok && i >= kNA) ok = warp_wait(&ctl.empty_acc[t], ph ^ 1, abort, wait_ns);
             if (!ok) break;
             const unsigned char *in = sm + C::OFF_IN + size_t(s_in) * kInBytes;
             unsigned char *ahi = sm + C::OFF_A + uint32_t(t) * 2 * kABytes;
@@ -488,9 +493,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const unsigned char *outb = sm + C::OFF_OUT;
         for (uint64_t i = 0; i < n_local; ++i) {
             const int t = int(i % kNA);
-            ok = warp_wait(&ctl.full_acc[t], uint32_t((i / kNA) & 1), abort);
+            ok = warp_wait(&ctl.full_acc[t], uint32_t((i / kNA) & 1), abort, wait_ns);
             // the split's row data of this tile (complete, as the MMAs that read its operands are)
-            if (ok) ok = warp_wait(&ctl.full_a[t], uint32_t((i / kNA) & 1), abort);
+            if (ok) ok = warp_wait(&ctl.full_a[t], uint32_t((i / kNA) & 1), abort, wait_ns);
             if (!ok) break;
             tc_fence_after();
             const int rho = 32 * qd + lane;
@@ -537,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 continue;
             }
-            if (i > 0 && !warp_wait(&ctl.epi_free, uint32_t((i - 1) & 1), abort)) {  // staging copied out
+            if (i > 0 && !warp_wait(&ctl.epi_free, uint32_t((i - 1) & 1), abort, wait_ns)) {  // staging copied out
                 ok = false;
                 break;
             }
@@ -551,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl.epi_full);
-            if (!warp_wait(&ctl.epi_full, uint32_t(i & 1), abort)) {
+            if (!warp_wait(&ctl.epi_full, uint32_t(i & 1), abort, wait_ns)) {
                 ok = false;
                 break;
             }
@@ -604,7 +609,8 @@ int fused_prepare() {
 size_t fused_rimg_halves(int k) { return 2 * size_t(4) << (2 * k); }  // 2 x (2^(k+1))^2
 
 int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const void *rimg_dev, int *status,
-                 cudaStream_t s) {
+                 cudaStream_t s, uint64_t wait_ns) {
+    if (wait_ns == 0) wait_ns = kWaitNs;
     if (int rc = fused_prepare()) return rc;
     const uint64_t ntiles = uint64_t(1) << (M - kFusedTileBits);
     uint64_t grid = uint64_t(num_sms());
@@ -613,7 +619,7 @@ int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const vo
     const float2 *i = static_cast<const float2 *>(src);
     const __half *r = static_cast<const __half *>(rimg_dev);
 #define QS_FUSED_LAUNCH(K, D) \
-    k_fused_tc<K, D><<<unsigned(grid), kThreads, Cfg<K, D>::SMEM, s>>>(o, i, d, r, ntiles, status)
+    k_fused_tc<K, D><<<unsigned(grid), kThreads, Cfg<K, D>::SMEM, s>>>(o, i, d, r, ntiles, status, wait_ns)
     switch (d.k * 2 + (d.direct ? 1 : 0)) {
         case 6: QS_FUSED_LAUNCH(3, false); break;
         case 7: QS_FUSED_LAUNCH(3, true); break;

@@ -1,10 +1,10 @@
 // Fidelity and norm with no device allocation at all.
 //
-// Some callers cannot allocate device memory: code that runs while its stream
-// is being captured into a CUDA graph (an allocation there breaks or
-// invalidates the capture), plugins inside a host application that hands out
-// all of the GPU's memory from its own pool, and latency-critical loops that
-// must never enter the allocator.  qsim_fidelity needs a qsim_state, and
+// Some callers cannot allocate device memory: plugins inside a host
+// application that hands out all of the GPU's memory from its own pool (a
+// cudaMalloc of their own would fail or break the host's accounting), and
+// latency-critical loops that must never enter the allocator, whose first
+// call could otherwise stall on it.  qsim_fidelity needs a qsim_state, and
 // creating one allocates the reduction's scratch; this file gives those
 // callers the same reduction over plain device pointers they already own.
 //
@@ -13,7 +13,11 @@
 // loads the library holds it (1.5 MiB) until the process exits.  In host
 // code the array's name is only a host-side stand-in, so its device address
 // is looked up once per device with cudaGetSymbolAddress and passed to the
-// kernels.
+// kernels.  The address is kept for the life of the process: it assumes the
+// device's primary context is not torn down (cudaDeviceReset) and re-created
+// in between.
+//
+// The call reads its result back to the host and waits for its stream.
 //
 // Every call shares the one array.  Each call writes every partial slot it
 // reads before reading it, so nothing has to start at zero, but two calls

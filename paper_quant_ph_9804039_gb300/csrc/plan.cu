@@ -72,6 +72,7 @@ struct qsim_plan {
     // stream (the serving loop), so creating and releasing a plan never
     // synchronises the device
     cudaStream_t alloc_stream = nullptr;
+    DevAllocator alloc{};  // device-memory functions in force when the plan was created
     qsim_plan_stats stats{};
     // CUDA graph of the launches for one (dst, src, stream)
     mutable cudaGraphExec_t gexec = nullptr;
@@ -1304,16 +1305,10 @@ double model_seconds(const qsim_plan *p, const std::vector<RegOp> &regops) {
 }
 
 int dev_alloc(const qsim_plan *p, void **dev, size_t bytes) {
-    if (p->alloc_stream) QS_CUDA(cudaMallocAsync(dev, bytes, p->alloc_stream));
-    else QS_CUDA(cudaMalloc(dev, bytes));
-    return QSIM_OK;
+    return dmalloc(p->alloc, dev, bytes, p->alloc_stream, "plan tables");
 }
 
-void dev_free(const qsim_plan *p, void *dev) {
-    if (!dev) return;
-    if (p->alloc_stream) cudaFreeAsync(dev, p->alloc_stream);
-    else cudaFree(dev);
-}
+void dev_free(const qsim_plan *p, void *dev, size_t bytes) { dfree(p->alloc, dev, bytes, p->alloc_stream); }
 
 int upload(const qsim_plan *p, void **dev, const void *host, size_t bytes, size_t *out_bytes) {
     *out_bytes = bytes;
@@ -1359,7 +1354,7 @@ int run_steps(const qsim_plan *p, void *dst, const void *src, cudaStream_t s, bo
             if (int rc = launch_perm(dst, first ? src : dst, p->M, p->prec, st.perm, s)) return rc;
         } else if (st.type == S_FUSED) {
             if (int rc = launch_fused(dst, first ? src : dst, p->M, st.f, static_cast<const __half *>(p->d_rimg) + st.rimg,
-                                      p->d_status, s))
+                                      p->d_status, s, uint64_t(p->opts.wait_us) * 1000u))
                 return rc;
         } else {
             if (first && src != dst) QS_CUDA(cudaMemcpyAsync(dst, src, vec_bytes, cudaMemcpyDeviceToDevice, s));
@@ -1390,7 +1385,7 @@ int smem_wavefronts(const uint32_t *addr, int width) { return wavefronts(addr, w
 namespace qs {
 
 int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, const qsim_opts *opts,
-                   cudaStream_t alloc_stream, qsim_plan **out) {
+                   cudaStream_t alloc_stream, const DevAllocator *alloc, qsim_plan **out) {
     if (!out) { set_error("out is NULL"); return QSIM_EINVAL; }
     if (M < 1 || M > QSIM_MAX_QUBITS) { set_error("M = %d outside [1, %d]", M, QSIM_MAX_QUBITS); return QSIM_EINVAL; }
     if (prec != QSIM_C64 && prec != QSIM_C128) { set_error("unknown precision %d", int(prec)); return QSIM_EINVAL; }
@@ -1398,6 +1393,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
     qsim_opts o{};
     if (opts) o = *opts;
     if (o.mode < QSIM_MODE_AUTO || o.mode > QSIM_MODE_FUSED) { set_error("unknown mode %d", o.mode); return QSIM_EINVAL; }
+    if (o.wait_us < 0) { set_error("wait_us %d is negative", o.wait_us); return QSIM_EINVAL; }
     if (o.tile_bits != 0 && (o.tile_bits < 6 || o.tile_bits > tile_max_bits(prec))) {
         set_error("tile_bits %d outside [6, %d]", o.tile_bits, tile_max_bits(prec));
         return QSIM_EINVAL;
@@ -1407,6 +1403,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
     p->prec = prec;
     p->opts = o;
     p->alloc_stream = alloc_stream;
+    p->alloc = alloc ? *alloc : current_allocator();
     p->gates.resize(n);
     for (size_t i = 0; i < n; ++i) {
         int rc = make_gate(M, gates[i].U, gates[i].target, gates[i].controls, gates[i].ncontrols, &p->gates[i]);
@@ -1617,6 +1614,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
     s.n_blocks = mode == QSIM_MODE_FUSED ? int32_t(p->steps.size()) : 0;
     s.algo_bytes = bytes;
     s.amp_updates = double(n) * std::ldexp(1.0, M);
+    s.table_bytes = int64_t(p->ops_bytes + p->runs_bytes + p->rimg_bytes + p->regops_bytes + p->rounds_bytes);
     *out = p;
     return QSIM_OK;
 }
@@ -1625,14 +1623,14 @@ void plan_release(qsim_plan *p) {
     if (!p) return;
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
-    dev_free(p, p->d_ops);
-    dev_free(p, p->d_runs);
-    dev_free(p, p->d_rimg);
+    dev_free(p, p->d_ops, p->ops_bytes);
+    dev_free(p, p->d_runs, p->runs_bytes);
+    dev_free(p, p->d_rimg, p->rimg_bytes);
     jit_release(p->jit_libs);
     p->jit_libs.clear();
-    dev_free(p, p->d_regops);
-    dev_free(p, p->d_rounds);
-    dev_free(p, p->d_status);
+    dev_free(p, p->d_regops, p->regops_bytes);
+    dev_free(p, p->d_rounds, p->rounds_bytes);
+    dev_free(p, p->d_status, sizeof(int));
     delete p;
 }
 
@@ -1642,7 +1640,7 @@ extern "C" {
 
 int qsim_plan_create(int M, qsim_prec prec, const qsim_gate *gates, size_t n, const qsim_opts *opts,
                      qsim_plan **out) {
-    return plan_create_on(M, prec, gates, n, opts, nullptr, out);
+    return plan_create_on(M, prec, gates, n, opts, nullptr, nullptr, out);
 }
 
 int qsim_plan_execute(const qsim_plan *p, qsim_state *dst, const qsim_state *src) {
@@ -1747,8 +1745,11 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
                     : "");
         } else if (st.type == S_FUSED) {
             add("step %zu FUSED k=%d unitary=%d runbits=%d qubits=", j, st.f.k, st.f.unitary, st.f.runbits);
-            for (int a = 0; a < st.f.k; ++a) add("%d ", __builtin_ctz(st.f.posA[1 << a]));
-            add("(tile positions)\n");
+            for (int a = 0; a < st.f.k; ++a) {  // tile index bit -> device qubit
+                const int b = __builtin_ctz(st.f.posA[1 << a]);
+                add("%d ", b < st.f.runbits ? b : st.f.rpos[b - st.f.runbits]);
+            }
+            add("\n");
         } else {
             add("step %zu TILE b=%d L=%d high=", j, st.d.b, st.d.L);
             for (int h = 0; h < st.d.nh; ++h) add("%d%s", st.d.hpos[h], h + 1 < st.d.nh ? "," : "");

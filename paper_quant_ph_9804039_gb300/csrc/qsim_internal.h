@@ -28,6 +28,20 @@ int cuda_fail(cudaError_t e, const char *what);  // records the message, returns
 
 int num_sms();  // streaming multiprocessors of the current device
 
+// ----------------------------------------------------------- device memory
+// The function pair in force when an object was created (qsim_set_allocator;
+// null = the CUDA runtime).  dmalloc returns QSIM_ENOMEM (message set) on
+// failure; with s != nullptr and no hook the runtime allocation is
+// stream-ordered (cudaMallocAsync / cudaFreeAsync on s).
+struct DevAllocator {
+    qsim_device_alloc_fn alloc;
+    qsim_device_free_fn free;
+    void *ctx;
+};
+DevAllocator current_allocator();
+int dmalloc(const DevAllocator &a, void **p, size_t bytes, cudaStream_t s, const char *what);
+void dfree(const DevAllocator &a, void *p, size_t bytes, cudaStream_t s);
+
 // ------------------------------------------------------------------- gates
 // Gate kinds, chosen from the matrix on the host:
 //   DENSE  : general 2x2
@@ -72,7 +86,9 @@ struct State {
     double *scratch;     // reduction partials; the last 4 doubles hold the result
     int scratch_blocks;  // partial slots (3 doubles each)
     cudaEvent_t ev;      // orders work across states' streams
+    DevAllocator alloc;  // the device-memory functions the state was created with
 };
+inline size_t state_scratch_bytes(int slots) { return (3 * size_t(slots) + 4) * sizeof(double); }
 
 inline size_t amp_bytes(qsim_prec p) { return p == QSIM_C64 ? 8 : 16; }
 
@@ -245,8 +261,9 @@ struct FusedDesc {
 };
 int fused_prepare();
 size_t fused_rimg_halves(int k);  // FP16 values of one block's R_hi + R_lo image
+// wait_ns bounds the kernel's pipeline waits (0 = 2 s); see k_fused_tc.cu.
 int launch_fused(void *dst, const void *src, int M, const FusedDesc &d, const void *rimg_dev, int *status,
-                 cudaStream_t s);
+                 cudaStream_t s, uint64_t wait_ns);
 
 // ------------------------------------------------------- qubit permutation
 // out[pi(i)] = in[i] for an involution pi of the qubit positions (see
@@ -280,10 +297,11 @@ struct qsim_state : qs::State {};
 
 namespace qs {
 // Plan creation whose device tables are allocated stream-ordered on
-// alloc_stream (nullptr: plain cudaMalloc), and release without a device
-// synchronisation: the caller guarantees that the plan's work has completed
-// or is ordered before alloc_stream's later work.
+// alloc_stream (nullptr: plain cudaMalloc) through `alloc` (nullptr: the
+// functions in force now), and release without a device synchronisation: the
+// caller guarantees that the plan's work has completed or is ordered before
+// alloc_stream's later work.
 int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, const qsim_opts *opts,
-                   cudaStream_t alloc_stream, qsim_plan **out);
+                   cudaStream_t alloc_stream, const DevAllocator *alloc, qsim_plan **out);
 void plan_release(qsim_plan *p);
 }  // namespace qs

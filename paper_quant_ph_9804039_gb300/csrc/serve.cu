@@ -73,7 +73,8 @@ struct qsim_server {
     uint64_t n_submitted = 0, n_completed = 0;
     int max_active = 0;
     bool stop = false;
-    cudaMemPool_t pool = nullptr;
+    cudaMemPool_t pool = nullptr;  // used when no allocator hook was set at creation
+    DevAllocator alloc{};          // the hook in force at creation, if any
     std::thread worker;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -97,12 +98,19 @@ size_t request_bytes(int M) { return 2 * (size_t(1) << M) * sizeof(float) * 2; }
 int start_request(qsim_server *srv, Slot *s) {
     const Request &r = s->req;
     const size_t vec = (size_t(1) << r.M) * 8;
-    for (int k = 0; k < 2; ++k)
-        QS_CUDA(cudaMallocFromPoolAsync(&s->amps[k], vec, srv->pool, s->stream));
+    for (int k = 0; k < 2; ++k) {
+        if (srv->alloc.alloc) {
+            if (int rc = dmalloc(srv->alloc, &s->amps[k], vec, s->stream, "served state")) return rc;
+        } else {
+            QS_CUDA(cudaMallocFromPoolAsync(&s->amps[k], vec, srv->pool, s->stream));
+        }
+    }
     qsim_opts po{srv->opts.mode, 0, 0, 0, 0};
-    if (int rc = plan_create_on(r.M, QSIM_C64, r.ideal.data(), r.ideal.size(), &po, s->stream, &s->plans[0]))
+    if (int rc = plan_create_on(r.M, QSIM_C64, r.ideal.data(), r.ideal.size(), &po, s->stream, &srv->alloc,
+                                &s->plans[0]))
         return rc;
-    if (int rc = plan_create_on(r.M, QSIM_C64, r.noisy.data(), r.noisy.size(), &po, s->stream, &s->plans[1]))
+    if (int rc = plan_create_on(r.M, QSIM_C64, r.noisy.data(), r.noisy.size(), &po, s->stream, &srv->alloc,
+                                &s->plans[1]))
         return rc;
     qsim_state st[2];
     for (int k = 0; k < 2; ++k) {
@@ -114,6 +122,7 @@ int start_request(qsim_server *srv, Slot *s) {
         st[k].scratch = s->scratch;
         st[k].scratch_blocks = kReduceSlots;
         st[k].ev = s->ev;
+        st[k].alloc = srv->alloc;
         if (int rc = launch_zero_state(s->amps[k], r.M, QSIM_C64, s->stream)) return rc;
         if (int rc = qsim_plan_execute(s->plans[k], &st[k], nullptr)) return rc;
     }
@@ -143,7 +152,10 @@ void retire(qsim_server *srv, Slot *s, std::vector<qsim_request_result> &out) {
     for (int k = 0; k < 2; ++k) {
         if (s->plans[k]) plan_release(s->plans[k]);
         s->plans[k] = nullptr;
-        if (s->amps[k]) cudaFreeAsync(s->amps[k], s->stream);
+        if (s->amps[k]) {
+            if (srv->alloc.free) dfree(srv->alloc, s->amps[k], (size_t(1) << s->req.M) * 8, s->stream);
+            else cudaFreeAsync(s->amps[k], s->stream);
+        }
         s->amps[k] = nullptr;
     }
     srv->bytes_in_use -= s->bytes;
@@ -243,6 +255,7 @@ int qsim_server_create(const qsim_server_opts *opts, qsim_server **out) {
         return rc;
     };
     if (cudaGetDevice(&srv->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaGetDevice"));
+    srv->alloc = current_allocator();
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -256,9 +269,11 @@ int qsim_server_create(const qsim_server_opts *opts, qsim_server **out) {
         srv->slots.push_back(s);
         cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMalloc(&s->scratch, (3 * size_t(kReduceSlots) + 4) * sizeof(double));
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_res, 4 * sizeof(double));
         if (e != cudaSuccess) return fail(cuda_fail(e, "server slot"));
+        if (int rc = dmalloc(srv->alloc, reinterpret_cast<void **>(&s->scratch), state_scratch_bytes(kReduceSlots),
+                             nullptr, "server slot scratch"))
+            return fail(rc);
     }
     if (int rc = tile_prepare(QSIM_C64)) return fail(rc);
     if (int rc = fused_prepare()) return fail(rc);
@@ -330,7 +345,7 @@ void qsim_server_destroy(qsim_server *srv) {
     if (srv->worker.joinable()) srv->worker.join();
     for (Slot *s : srv->slots) {
         if (s->stream) cudaStreamSynchronize(s->stream);
-        if (s->scratch) cudaFree(s->scratch);
+        dfree(srv->alloc, s->scratch, state_scratch_bytes(kReduceSlots), nullptr);
         if (s->h_res) cudaFreeHost(s->h_res);
         if (s->ev) cudaEventDestroy(s->ev);
         if (s->stream) cudaStreamDestroy(s->stream);

@@ -200,6 +200,8 @@ struct qsim_traj_plan {
     cudaKernel_t jit_k = nullptr;
     std::string log;      // why the register kernel could not be built
     std::string tune;     // the autotuner's record
+    DevAllocator alloc{};  // device-memory functions in force when the plan was created
+    size_t passes_bytes = 0, ops_bytes = 0, work_bytes = 0;
 };
 
 namespace {
@@ -299,16 +301,21 @@ int build_passes(qsim_traj_plan *p, const std::vector<Gate> &gates, const double
 }
 
 int upload_tables(qsim_traj_plan *p) {
-    if (p->d_passes) cudaFree(p->d_passes);
-    if (p->d_ops) cudaFree(p->d_ops);
+    dfree(p->alloc, p->d_passes, p->passes_bytes, nullptr);
+    dfree(p->alloc, p->d_ops, p->ops_bytes, nullptr);
     p->d_passes = nullptr;
     p->d_ops = nullptr;
-    QS_CUDA(cudaMalloc(&p->d_passes, p->passes.size() * sizeof(TilePassDesc)));
-    QS_CUDA(cudaMemcpy(p->d_passes, p->passes.data(), p->passes.size() * sizeof(TilePassDesc),
-                       cudaMemcpyHostToDevice));
+    p->passes_bytes = p->passes.size() * sizeof(TilePassDesc);
+    p->ops_bytes = p->ops.size() * sizeof(TrajOp);
+    if (int rc = dmalloc(p->alloc, reinterpret_cast<void **>(&p->d_passes), p->passes_bytes, nullptr,
+                         "trajectory pass table"))
+        return rc;
+    QS_CUDA(cudaMemcpy(p->d_passes, p->passes.data(), p->passes_bytes, cudaMemcpyHostToDevice));
     if (!p->ops.empty()) {
-        QS_CUDA(cudaMalloc(&p->d_ops, p->ops.size() * sizeof(TrajOp)));
-        QS_CUDA(cudaMemcpy(p->d_ops, p->ops.data(), p->ops.size() * sizeof(TrajOp), cudaMemcpyHostToDevice));
+        if (int rc = dmalloc(p->alloc, reinterpret_cast<void **>(&p->d_ops), p->ops_bytes, nullptr,
+                             "trajectory op table"))
+            return rc;
+        QS_CUDA(cudaMemcpy(p->d_ops, p->ops.data(), p->ops_bytes, cudaMemcpyHostToDevice));
     }
     return QSIM_OK;
 }
@@ -424,6 +431,7 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
             if (!std::isfinite(err_axis[3 * i + k])) { set_error("axis %zu not finite", i); return QSIM_EINVAL; }
     }
     qsim_traj_plan *p = new qsim_traj_plan();
+    p->alloc = current_allocator();
     p->M = M;
     p->n = int(n);
     p->max_T = max_T;
@@ -452,11 +460,18 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
     p->grid = num_sms() * per_sm;
     if (p->grid > max_T) p->grid = max_T;
     {
-        cudaError_t e = cudaMalloc(&p->d_work, (size_t(p->grid) << M) * sizeof(float2));
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_eps, size_t(max_T) * std::max<size_t>(n, 1) * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_F, size_t(max_T) * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(unsigned));
-        if (e == cudaSuccess) e = cudaMallocHost(&p->h_eps, size_t(max_T) * std::max<size_t>(n, 1) * sizeof(double));
+        const size_t n_eps = size_t(max_T) * std::max<size_t>(n, 1);
+        p->work_bytes = (size_t(p->grid) << M) * sizeof(float2);
+        if ((rc = dmalloc(p->alloc, reinterpret_cast<void **>(&p->d_work), p->work_bytes, nullptr,
+                          "trajectory workspaces")) ||
+            (rc = dmalloc(p->alloc, reinterpret_cast<void **>(&p->d_eps), n_eps * sizeof(double), nullptr,
+                          "trajectory errors")) ||
+            (rc = dmalloc(p->alloc, reinterpret_cast<void **>(&p->d_F), size_t(max_T) * sizeof(double), nullptr,
+                          "trajectory fidelities")) ||
+            (rc = dmalloc(p->alloc, reinterpret_cast<void **>(&p->d_counter), sizeof(unsigned), nullptr,
+                          "trajectory counter")))
+            return fail(rc);
+        cudaError_t e = cudaMallocHost(&p->h_eps, n_eps * sizeof(double));
         if (e == cudaSuccess) e = cudaMallocHost(&p->h_F, size_t(max_T) * sizeof(double));
         if (e != cudaSuccess) return fail(cuda_fail(e, "trajectory buffers"));
     }
@@ -630,13 +645,13 @@ void qsim_traj_plan_destroy(qsim_traj_plan *p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     jit_release(p->jit_lib);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    cudaFree(p->d_passes);
-    cudaFree(p->d_ops);
-    cudaFree(p->d_ideal);
-    cudaFree(p->d_work);
-    cudaFree(p->d_eps);
-    cudaFree(p->d_F);
-    cudaFree(p->d_counter);
+    dfree(p->alloc, p->d_passes, p->passes_bytes, nullptr);
+    dfree(p->alloc, p->d_ops, p->ops_bytes, nullptr);
+    dfree(p->alloc, p->d_ideal, (size_t(1) << p->M) * sizeof(float2), nullptr);
+    dfree(p->alloc, p->d_work, p->work_bytes, nullptr);
+    dfree(p->alloc, p->d_eps, size_t(p->max_T) * std::max<size_t>(size_t(p->n), 1) * sizeof(double), nullptr);
+    dfree(p->alloc, p->d_F, size_t(p->max_T) * sizeof(double), nullptr);
+    dfree(p->alloc, p->d_counter, sizeof(unsigned), nullptr);
     if (p->h_eps) cudaFreeHost(p->h_eps);
     if (p->h_F) cudaFreeHost(p->h_F);
     if (p->stream) cudaStreamDestroy(p->stream);

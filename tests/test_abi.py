@@ -83,3 +83,12 @@ def test_async_copy_rejects_null_on_host():
     lib = qs.load_library()
     assert lib.qsim_set_state_async(None, None, 0) == qs.QSIM_EINVAL
     assert b"NULL" in lib.qsim_last_error()
+
+
+def test_set_allocator_host_checks():
+    """qsim_set_allocator takes both functions or neither (no CUDA call)."""
+    lib = qs.load_library()
+    fa = qs.ALLOC_FN(lambda n, s, c: None)
+    assert lib.qsim_set_allocator(ctypes.cast(fa, ctypes.c_void_p), None, None) == qs.QSIM_EINVAL
+    assert b"both" in lib.qsim_last_error()
+    assert lib.qsim_set_allocator(None, None, None) == qs.QSIM_OK

@@ -1,8 +1,8 @@
 """qsim_fidelity_noalloc: the fidelity and norm for callers that cannot
-allocate device memory (work captured into a CUDA graph, plugins whose host
-application owns all GPU memory, latency-critical loops).  It takes raw
-device pointers and keeps its scratch in a fixed device array, so it must
-give what qsim_fidelity gives, call after call.
+allocate device memory (plugins whose host application owns all GPU memory
+through its own pool, latency-critical loops that must never enter the
+allocator).  It takes raw device pointers and keeps its scratch in a fixed
+device array, so it must give what qsim_fidelity gives, call after call.
 
 This file sorts last so that a run stopping at its first failure has already
 run every other test; it also passes on its own in a fresh process.
