@@ -635,6 +635,7 @@ def run_ours(args, rank, world, local):
         stream = torch.cuda.current_stream()
         result["single_gate"] = bench_single_gate(stream)
         result["batched"] = bench_trajectories(world, result["clocks"].get("sm_mhz"))
+        result["subspace"] = bench_subspace(world, stream)
         result["serving"] = bench_serving(args.serve_requests, world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -738,6 +739,54 @@ def bench_trajectories(world, sm_mhz=None):
             "sequential_unfused_trajectories_per_s": 1.0 / dts,
             "sequential_sample": f"{ns} trajectories, one gate per launch, plans made before the timed loop",
             "speedup_of_sequential": (T / dt) * dts}
+
+
+def bench_subspace(world, stream):
+    """Touched-qubit subspace (Section 3.2, EQ 6): a circuit that touches its
+    30 qubits one at a time (Hadamards on 4, then per further qubit a CNOT
+    onto it and 16 gates among the touched ones; over-rotation sigma=1e-3),
+    from |0...0>, complex64.  One step = the error-free and the noisy circuit
+    and F.  The flat plans run every gate on all 2^30 amplitudes; the
+    subspace plans run each segment on the prefix its touched qubits span and
+    restore the qubit order at the end."""
+    import torch
+    import paper_quant_ph_9804039_gb300 as qs
+    from workloads import generators as W
+    M = 30
+    c = W.circuit_gradual(M, start=4, per_qubit=16)
+    n = len(c["ideal"])
+    a = qs.State(M, stream=stream)
+    b = qs.State(M, stream=stream)
+    out = {"workload": "gradual-m30-c64", "M": M, "gates_per_circuit": n}
+    for name, sub in (("flat", False), ("subspace", True)):
+        t = time.perf_counter()
+        pi = qs.Plan(M, c["ideal"], mode="tiled", specialize=True, subspace=sub)
+        pn = qs.Plan(M, c["noisy"], mode="tiled", specialize=True, subspace=sub)
+        t = time.perf_counter() - t
+        res = {}
+
+        def step():
+            if not sub:
+                a.reset()
+                b.reset()
+            pi.execute(a)
+            pn.execute(b)
+            res["F"] = qs.fidelity(a, b)
+
+        ms = _events_ms(step, 3, stream)
+        entry = {"ms_per_step": ms, "amp_updates_per_s": world * 2.0 * n * float(1 << M) / (ms / 1e3),
+                 "passes_per_circuit": pn.stats()["n_passes"], "F": res["F"][0], "norm": res["F"][1],
+                 "plan_create_s": round(t, 3)}
+        if sub:
+            line = pn.describe().split("subspace: ")[1].splitlines()[0]
+            entry["planned"] = line
+        out[name] = entry
+        del pi, pn
+    out["speedup"] = out["flat"]["ms_per_step"] / out["subspace"]["ms_per_step"]
+    out["F_difference"] = abs(out["flat"]["F"] - out["subspace"]["F"])
+    del a, b
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_serving(n_requests, world):

@@ -98,6 +98,16 @@ typedef struct qsim_opts {
                          * drains its copies and MMAs in flight, with the full 2 s bound, and
                          * frees its tensor memory) and qsim_plan_status then reports
                          * QSIM_ETIMEOUT; the state is undefined.  For failure-detection tests */
+    int32_t subspace;   /* 1: the plan applies the circuit to |0...0> (the input of qsim_plan_execute is
+                         * not read; dst is overwritten) and runs each gate only on the amplitudes
+                         * the qubits touched so far can make nonzero (Section 3.2, Figure 7: state
+                         * values are allocated once a gate first uses their qubit; EQ 6): qubits
+                         * are renumbered in the order gates first touch them, gates with a control
+                         * no gate has touched are left out, and the gates between two first touches
+                         * run, in `mode`, on the first 2^(qubits touched) amplitudes; at the end at
+                         * most two in-place permutation passes restore the qubit order.  The result
+                         * equals the flat plan's up to rounding.  qsim_plan_describe lists the
+                         * segments.  Per-launch timing (qsim_plan_set_timing) is not recorded */
 } qsim_opts;
 
 /* Counts describing one execution of a plan. */
@@ -410,6 +420,28 @@ void qsim_server_destroy(qsim_server *srv);
 typedef void *(*qsim_device_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx);
 typedef void (*qsim_device_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *ctx);
 int qsim_set_allocator(qsim_device_alloc_fn alloc, qsim_device_free_fn free, void *ctx);
+
+/* ----------------------------------------------------------- autotuning */
+
+/* The tuning cache (outside the paper; execution choices, not results).
+ * QSIM_MODE_AUTO picks among tile passes of 2^12 or 2^11 amplitudes and fused
+ * blocks of width 5, 4 or 3 by a time model of the planned passes whose rates
+ * are measured on the device (a light and a heavy tile pass, a permutation
+ * pass, one fused block of each width on and off qubits 0..4, on a 26-qubit
+ * state: about a second, once per device, precision and tile-kernel kind);
+ * trajectory plans time their candidate kernels on a short batch.  Both are
+ * kept in memory and, when a cache file is set, in that JSON file, which later
+ * processes read instead of measuring again.  path = NULL keeps them in memory
+ * only (the default unless the environment variable QSIM_TUNE_CACHE names a
+ * file).  Setting the path drops what is in memory. */
+int qsim_tune_set_cache(const char *path);
+
+/* The measured rates AUTO uses for this precision and tile-kernel kind
+ * (specialize != 0: the NVRTC-generated passes), measuring them now unless
+ * the cache holds them, as a JSON object in buf (at most len - 1 characters
+ * and a NUL; *needed = the full length + 1): bandwidths in bytes/s, the FMA
+ * rate in FMA-equivalents/s, and where they came from. */
+int qsim_tune_rates(int prec, int specialize, char *buf, int64_t len, int64_t *needed);
 
 /* ---------------------------------------------------------------- misc */
 

@@ -44,7 +44,8 @@ class QsimError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("fuse_k", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32), ("wait_us", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32), ("wait_us", ctypes.c_int32),
+                ("subspace", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -132,6 +133,9 @@ SIGNATURES = [
     ("qsim_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
     ("qsim_server_destroy", None, [_vp]),
     ("qsim_set_allocator", ctypes.c_int, [_vp, _vp, _vp]),
+    ("qsim_tune_set_cache", ctypes.c_int, [ctypes.c_char_p]),
+    ("qsim_tune_rates", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_int64)]),
     ("qsim_last_error", ctypes.c_char_p, []),
     ("qsim_version", ctypes.c_char_p, []),
 ]
@@ -158,7 +162,30 @@ def load_library(build_if_missing: bool = True):
         fn.restype = res
         fn.argtypes = args
     _lib = lib
+    if not os.environ.get("QSIM_TUNE_CACHE"):
+        lib.qsim_tune_set_cache(DEFAULT_TUNE_CACHE.encode())
     return lib
+
+
+# the tuning cache next to the built library (ignored by version control)
+DEFAULT_TUNE_CACHE = os.path.join(os.path.dirname(_LIB_PATH), "qsim_tune.json")
+
+
+def set_tune_cache(path):
+    """qsim_tune_set_cache: the JSON file of measured rates and timed
+    trajectory configurations (None: memory only)."""
+    _check(load_library().qsim_tune_set_cache(None if path is None else str(path).encode()))
+
+
+def tune_rates(prec="c64", specialize=True) -> dict:
+    """The measured rates QSIM_MODE_AUTO uses (qsim_tune_rates)."""
+    import json
+    lib = load_library()
+    n = ctypes.c_int64(0)
+    _check(lib.qsim_tune_rates(_prec(prec), int(bool(specialize)), None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(int(n.value))
+    _check(lib.qsim_tune_rates(_prec(prec), int(bool(specialize)), buf, n.value, ctypes.byref(n)))
+    return json.loads(buf.value.decode())
 
 
 def _check(rc: int):
@@ -177,9 +204,10 @@ def _records(gates) -> np.ndarray:
     return np.ascontiguousarray(gates, dtype=GATE_DTYPE)
 
 
-def _opts(mode="auto", fuse_k=0, tile_bits=0, use_graph=False, specialize=False, wait_us=0) -> Opts:
+def _opts(mode="auto", fuse_k=0, tile_bits=0, use_graph=False, specialize=False, wait_us=0, subspace=False) -> Opts:
     m = _MODES[mode] if isinstance(mode, str) else int(mode)
-    return Opts(m, int(fuse_k), int(tile_bits), int(bool(use_graph)), int(bool(specialize)), int(wait_us))
+    return Opts(m, int(fuse_k), int(tile_bits), int(bool(use_graph)), int(bool(specialize)), int(wait_us),
+                int(bool(subspace)))
 
 
 def _torch():
@@ -306,13 +334,13 @@ class Plan:
     """A compiled circuit for states of M qubits (qsim_plan_create)."""
 
     def __init__(self, M: int, gates, prec="c64", mode="auto", fuse_k=0, tile_bits=0, use_graph=False,
-                 specialize=False, wait_us=0):
+                 specialize=False, wait_us=0, subspace=False):
         lib = load_library()
         self.M = int(M)
         self.prec = _prec(prec)
         g = _records(gates)
         self.n_gates = len(g)
-        o = _opts(mode, fuse_k, tile_bits, use_graph, specialize, wait_us)
+        o = _opts(mode, fuse_k, tile_bits, use_graph, specialize, wait_us, subspace)
         h = _vp()
         _check(lib.qsim_plan_create(self.M, self.prec, _vp(g.ctypes.data), len(g), ctypes.byref(o), ctypes.byref(h)))
         self._h = h

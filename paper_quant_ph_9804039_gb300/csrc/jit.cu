@@ -643,6 +643,8 @@ bool compile_cubin(const std::string &src, const char *name, std::vector<char> *
 
 }  // namespace
 
+bool jit_available() { return nvrtc().ok; }
+
 // One program per pass, compiled on a pool of host threads (compile time
 // grows faster than linearly with the program, and passes are independent),
 // each loaded as its own library.

@@ -84,6 +84,17 @@ struct qsim_plan {
     mutable std::vector<cudaEvent_t> ev_pool;
     mutable size_t ev_used = 0;
     mutable int64_t timed_execs = 0;
+    // touched-qubit subspace (qsim_opts.subspace): the circuit from |0...0>
+    // runs as segments, each a child plan on the 2^seg_M[i] amplitudes of the
+    // vector's prefix, then `relabel` moves the touched qubits from the order
+    // in which they were first touched to their own positions
+    bool subspace = false;
+    std::vector<qsim_plan *> seg_plans;
+    std::vector<int> seg_M;
+    qsim_plan *relabel = nullptr;
+    std::vector<int> sub_order;      // physical qubits in the order first touched
+    int64_t sub_skipped = 0;         // gates left out (a control never touched)
+    double sub_amp_updates = 0;      // sum over segments of gates x 2^seg_M
 };
 
 namespace {
@@ -1235,18 +1246,20 @@ void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
 }
 
 // ------------------------------------------------------------ AUTO mode
-// A rough time model for choosing between the tile passes and the fused
-// tensor-core blocks (complex64): a pass or a block moves 16 * 2^M bytes; a
-// register pass also spends the arithmetic of its ops, at a sustained FP32
-// rate; a fused block runs at a fixed fraction of the memory bandwidth.  The
-// constants are this simulator's measurements on GB300 (tile passes at copy
-// speed ~6.0 TB/s, fused blocks ~5.0 TB/s, register-pass arithmetic at ~2.2e13
-// FMA/s, permutation passes ~3.6 TB/s).
-constexpr double kModelPassBw = 6.0e12, kModelFusedBw = 5.0e12, kModelPermBw = 3.6e12, kModelFma = 2.2e13;
+// A time model for choosing the execution form (complex64): a pass or a
+// block moves 16 * 2^M bytes; a register pass also spends the arithmetic of
+// its ops; a permutation pass and a fused block of width k run at their own
+// bandwidths.  The rates are measured on the device (tune.cu: a light and a
+// heavy tile pass, a permutation pass, one fused block of each width on and
+// off qubits 0..4) and kept in the tuning cache.
 
-int count_fused_blocks(const std::vector<Gate> &gates, int k) {
+// Seconds of the fused blocks of width k for these gates (the grouping of
+// plan_fused, without building the matrices).
+double model_fused(const std::vector<Gate> &gates, int k, int M, const ModelRates &r, int *nblocks) {
     std::vector<int> rem(gates.size());
     for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
+    const double bytes = 16.0 * std::ldexp(1.0, M);
+    double t = 0;
     int blocks = 0;
     while (!rem.empty()) {
         uint64_t defN = 0, defA = 0, Q = 0;
@@ -1263,10 +1276,13 @@ int count_fused_blocks(const std::vector<Gate> &gates, int k) {
                 defA |= A;
             }
         }
+        for (int q = 0; q < M && __builtin_popcountll(Q) < k; ++q) Q |= bit(q);
+        t += bytes / ((Q & 31u) ? r.fused_staged[k] : r.fused_direct[k]);
         ++blocks;
         rem.swap(keep);
     }
-    return blocks;
+    if (nblocks) *nblocks = blocks;
+    return t;
 }
 
 // FMA-equivalent operations per amplitude of one register op.
@@ -1283,23 +1299,34 @@ double regop_cost(const RegOp &op, int S) {
     return 8.0 * touched;
 }
 
-double model_seconds(const qsim_plan *p, const std::vector<RegOp> &regops) {
+double step_fma(const Step &st, const std::vector<RegOp> &regops) {
+    if (st.type != S_TILE) return 0.0;
+    double fma = 0;
+    const int S = 1 << std::max(0, st.d.b - kRegThreadBits);
+    if (st.d.round_count > 0)
+        for (int j = 0; j < st.d.op_count; ++j) fma += regop_cost(regops[size_t(st.d.op_begin + j)], S);
+    else
+        fma = 16.0 * double(st.d.op_count);
+    return fma;
+}
+
+}  // namespace
+
+double qs::plan_model_fma(const qsim_plan *p) {
+    double f = 0;
+    for (const Step &st : p->steps) f += step_fma(st, p->h_regops);
+    return f;
+}
+
+namespace {
+
+double model_seconds(const qsim_plan *p, const std::vector<RegOp> &regops, const ModelRates &r) {
     const double N = std::ldexp(1.0, p->M);
     double t = 0;
     for (const Step &st : p->steps) {
-        if (st.type == S_PERM) {
-            t += 16.0 * N / kModelPermBw;
-        } else if (st.type == S_TILE) {
-            double fma = 0;
-            const int S = 1 << std::max(0, st.d.b - kRegThreadBits);
-            if (st.d.round_count > 0)
-                for (int j = 0; j < st.d.op_count; ++j) fma += regop_cost(regops[size_t(st.d.op_begin + j)], S);
-            else
-                fma = 16.0 * double(st.d.op_count);
-            t += std::max(16.0 * N / kModelPassBw, fma * N / kModelFma);
-        } else if (st.type == S_FUSED) {
-            t += 16.0 * N / kModelFusedBw;
-        }
+        if (st.type == S_PERM) t += 16.0 * N / r.perm_bw;
+        else if (st.type == S_TILE) t += std::max(16.0 * N / r.pass_bw, step_fma(st, regops) * N / r.fma_rate);
+        else if (st.type == S_FUSED) t += 16.0 * N / r.fused_direct[st.f.k];
     }
     return t;
 }
@@ -1384,6 +1411,236 @@ int smem_wavefronts(const uint32_t *addr, int width) { return wavefronts(addr, w
 
 namespace qs {
 
+// ------------------------------------------------ touched-qubit subspace
+// Section 3.2 (Figure 7) allocates the state values of a qubit only once a
+// gate first uses it: every amplitude whose untouched qubits are not all 0
+// is zero, and a transformation on zero values changes nothing (EQ 6 sums
+// the cost of each step over the qubits used so far).  Here a circuit applied
+// to |0...0> is planned the same way on a flat vector.  Qubits are numbered
+// in the order a gate first touches them (virtual position v = the v-th
+// qubit touched), so the nonzero amplitudes are the first 2^|T| of the
+// vector, T the touched set, and gates act on that prefix only:
+//   - a gate with a control outside T is the identity (the control is 0);
+//   - a gate on a target outside T with U10 = 0 leaves the target at 0 and
+//     multiplies the amplitudes whose controls are 1 by U00: it becomes
+//     diag(1, U00) on a control (controlled by the other), or, with no
+//     control, the factor U00 on the whole prefix (kept aside while T is
+//     empty and folded into the first gate that touches a qubit);
+//   - any other gate on a target outside T adds the target to T, doubling
+//     the prefix; its new half is zero because the vector starts at |0...0>.
+// Gates between two growths form a segment, run by a child plan on the
+// prefix; short segments (fewer than kSubMinGates gates, or a prefix below
+// 2^kSubMinBits amplitudes) are merged into the next one, whose larger
+// prefix they run on unchanged (the extra amplitudes are zero).  At the end
+// a permutation plan moves virtual position v to physical qubit order[v]
+// (the untouched qubits, all 0, after the touched ones in ascending order):
+// a product of two involutions, each one in-place permutation pass.
+constexpr int kSubMinBits = 16;
+constexpr size_t kSubMinGates = 8;
+
+// Two involutions s1, s2 with s2(s1(v)) = pi(v): on each cycle
+// c_0 -> c_1 -> ... of pi, s1(c_i) = c_{-i} and s2(c_i) = c_{1-i}.
+void split_involutions(const std::vector<int> &pi, std::vector<int> &s1, std::vector<int> &s2) {
+    const int M = int(pi.size());
+    s1.assign(M, 0);
+    s2.assign(M, 0);
+    std::vector<char> seen(M, 0);
+    for (int v = 0; v < M; ++v) {
+        if (seen[v]) continue;
+        std::vector<int> cyc;
+        for (int c = v; !seen[c]; c = pi[c]) {
+            seen[c] = 1;
+            cyc.push_back(c);
+        }
+        const int k = int(cyc.size());
+        for (int i = 0; i < k; ++i) {
+            s1[cyc[i]] = cyc[(k - i) % k];
+            s2[cyc[i]] = cyc[(k + 1 - i) % k];
+        }
+    }
+}
+
+int plan_relabel(const qsim_plan *parent, const std::vector<int> &pi, qsim_plan **out) {
+    const int M = parent->M;
+    qsim_plan *r = new qsim_plan();
+    r->M = M;
+    r->prec = parent->prec;
+    r->mode = QSIM_MODE_TILED;
+    r->alloc_stream = parent->alloc_stream;
+    r->alloc = parent->alloc;
+    std::vector<int> s1, s2;
+    split_involutions(pi, s1, s2);
+    for (const std::vector<int> *s : {&s1, &s2}) {
+        bool ident = true;
+        for (int v = 0; v < M; ++v) ident = ident && (*s)[v] == v;
+        if (ident) continue;
+        Step st{};
+        st.type = S_PERM;
+        st.perm = perm_desc(*s, M, parent->prec);
+        st.bytes = 2.0 * std::ldexp(1.0, M) * double(amp_bytes(parent->prec));
+        r->steps.push_back(st);
+    }
+    if (int rc = dev_alloc(r, reinterpret_cast<void **>(&r->d_status), sizeof(int))) {
+        plan_release(r);
+        return rc;
+    }
+    cudaError_t e = r->alloc_stream ? cudaMemsetAsync(r->d_status, 0, sizeof(int), r->alloc_stream)
+                                    : cudaMemset(r->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        plan_release(r);
+        return cuda_fail(e, "relabel status word");
+    }
+    double bytes = 0;
+    for (const Step &st : r->steps) bytes += st.bytes;
+    r->stats.n_passes = r->stats.n_launches = int64_t(r->steps.size());
+    r->stats.mode = QSIM_MODE_TILED;
+    r->stats.algo_bytes = bytes;
+    *out = r;
+    return QSIM_OK;
+}
+
+qsim_gate gate_record(const double *U, int t, int nc, int c0, int c1) {
+    qsim_gate g{};
+    for (int k = 0; k < 8; ++k) g.U[k] = U[k];
+    g.target = t;
+    g.ncontrols = nc;
+    g.controls[0] = c0;
+    g.controls[1] = c1;
+    return g;
+}
+
+int plan_subspace(qsim_plan *p) {
+    const int M = p->M;
+    std::vector<int> virt(M, -1);
+    std::vector<int> &order = p->sub_order;
+    double scale[2] = {1.0, 0.0};  // factor kept aside while nothing is touched
+    std::vector<std::vector<qsim_gate>> seg(1);
+    std::vector<int> segM(1, 0);
+    for (const Gate &g : p->gates) {
+        bool live = true;
+        for (int c = 0; c < g.nc; ++c) live = live && virt[g.c[c]] >= 0;
+        if (!live) {
+            ++p->sub_skipped;
+            continue;
+        }
+        const double *U = g.U;
+        const int vc0 = g.nc > 0 ? virt[g.c[0]] : 0, vc1 = g.nc > 1 ? virt[g.c[1]] : 0;
+        if (virt[g.t] < 0 && U[4] == 0.0 && U[5] == 0.0) {  // target stays 0: factor U00 where the controls are 1
+            if (U[0] == 1.0 && U[1] == 0.0) {
+                ++p->sub_skipped;
+                continue;
+            }
+            if (g.nc == 0 && order.empty()) {
+                const double re = scale[0] * U[0] - scale[1] * U[1], im = scale[0] * U[1] + scale[1] * U[0];
+                scale[0] = re;
+                scale[1] = im;
+                continue;
+            }
+            const double one[2] = {1.0, 0.0};
+            const double *d0 = g.nc == 0 ? U : one;
+            const double D[8] = {d0[0], d0[1], 0, 0, 0, 0, U[0], U[1]};
+            if (g.nc == 0) seg.back().push_back(gate_record(D, 0, 0, 0, 0));
+            else seg.back().push_back(gate_record(D, vc0, g.nc - 1, vc1, 0));
+            continue;
+        }
+        double V[8];
+        for (int k = 0; k < 8; ++k) V[k] = U[k];
+        if (virt[g.t] < 0) {  // the target joins the touched set: a new segment on a prefix twice as long
+            if (!seg.back().empty()) {
+                seg.emplace_back();
+                segM.push_back(0);
+            }
+            virt[g.t] = int(order.size());
+            order.push_back(g.t);
+            if (order.size() == 1 && (scale[0] != 1.0 || scale[1] != 0.0)) {  // the first touching gate has no control
+                for (int k = 0; k < 8; k += 2) {
+                    V[k] = scale[0] * U[k] - scale[1] * U[k + 1];
+                    V[k + 1] = scale[0] * U[k + 1] + scale[1] * U[k];
+                }
+                scale[0] = 1.0;
+                scale[1] = 0.0;
+            }
+        }
+        segM.back() = int(order.size());
+        seg.back().push_back(gate_record(V, virt[g.t], g.nc, vc0, vc1));
+    }
+    if (order.empty() && (scale[0] != 1.0 || scale[1] != 0.0)) {  // nothing touched: the factor on amplitude 0
+        const double D[8] = {scale[0], scale[1], 0, 0, 0, 0, scale[0], scale[1]};
+        seg.back().push_back(gate_record(D, 0, 0, 0, 0));
+        segM.back() = 1;
+    }
+    // merge short segments into the next (its prefix holds theirs)
+    std::vector<std::vector<qsim_gate>> mseg;
+    std::vector<int> mM;
+    for (size_t i = 0; i < seg.size(); ++i) {
+        if (seg[i].empty()) continue;
+        if (!mseg.empty() && (mM.back() < kSubMinBits || mseg.back().size() < kSubMinGates)) {
+            mseg.back().insert(mseg.back().end(), seg[i].begin(), seg[i].end());
+            mM.back() = segM[i];
+        } else {
+            mseg.push_back(seg[i]);
+            mM.push_back(segM[i]);
+        }
+    }
+    qsim_opts co = p->opts;
+    co.subspace = 0;
+    for (size_t i = 0; i < mseg.size(); ++i) {
+        const int Ms = std::max(1, mM[i]);
+        qsim_plan *c = nullptr;
+        if (int rc = plan_create_on(Ms, p->prec, mseg[i].data(), mseg[i].size(), &co, p->alloc_stream, &p->alloc, &c))
+            return rc;
+        p->seg_plans.push_back(c);
+        p->seg_M.push_back(Ms);
+        p->sub_amp_updates += double(mseg[i].size()) * std::ldexp(1.0, Ms);
+    }
+    std::vector<int> pi(M);
+    std::vector<char> used(M, 0);
+    for (size_t v = 0; v < order.size(); ++v) {
+        pi[v] = order[v];
+        used[order[v]] = 1;
+    }
+    for (int q = 0, v = int(order.size()); q < M; ++q)
+        if (!used[q]) pi[v++] = q;
+    bool ident = true;
+    for (int v = 0; v < M; ++v) ident = ident && pi[v] == v;
+    if (!ident)
+        if (int rc = plan_relabel(p, pi, &p->relabel)) return rc;
+    p->subspace = true;
+    p->mode = p->opts.mode;
+    qsim_plan_stats &s = p->stats;
+    s.n_gates = int64_t(p->gates.size());
+    s.mode = p->opts.mode;
+    s.algo_bytes = std::ldexp(1.0, M) * double(amp_bytes(p->prec));  // the initial |0...0>
+    s.n_passes = s.n_launches = 1;
+    for (qsim_plan *c : p->seg_plans) {
+        s.n_passes += c->stats.n_passes;
+        s.n_launches += c->stats.n_launches;
+        s.algo_bytes += c->stats.algo_bytes;
+        s.table_bytes += c->stats.table_bytes;
+    }
+    if (p->relabel) {
+        s.n_passes += p->relabel->stats.n_passes;
+        s.n_launches += p->relabel->stats.n_launches;
+        s.algo_bytes += p->relabel->stats.algo_bytes;
+    }
+    s.amp_updates = double(p->gates.size()) * std::ldexp(1.0, M);
+    return QSIM_OK;
+}
+
+// dst := circuit(|0...0>): zero the vector, run the segments on their
+// prefixes, move the qubits to their own positions.
+int run_subspace(const qsim_plan *p, qsim_state *dst) {
+    if (int rc = launch_zero_state(dst->amps, p->M, p->prec, dst->stream)) return rc;
+    for (size_t i = 0; i < p->seg_plans.size(); ++i) {
+        qsim_state pre = *dst;
+        pre.M = p->seg_M[i];
+        if (int rc = qsim_plan_execute(p->seg_plans[i], &pre, nullptr)) return rc;
+    }
+    if (p->relabel)
+        if (int rc = qsim_plan_execute(p->relabel, dst, nullptr)) return rc;
+    return QSIM_OK;
+}
+
 int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, const qsim_opts *opts,
                    cudaStream_t alloc_stream, const DevAllocator *alloc, qsim_plan **out) {
     if (!out) { set_error("out is NULL"); return QSIM_EINVAL; }
@@ -1420,39 +1677,82 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
         delete p;
         return QSIM_EINVAL;
     }
-    int mode = o.mode == QSIM_MODE_AUTO ? QSIM_MODE_TILED : o.mode;
-    if (o.mode == QSIM_MODE_AUTO && prec == QSIM_C64 && M >= 20) {
-        // plan the tile passes on a scratch plan (host only), estimate both forms
-        qsim_plan scratch;
-        scratch.M = M;
-        scratch.prec = prec;
-        scratch.gates = p->gates;
-        split_row_phases(scratch.gates);
-        const int b = std::min(o.tile_bits ? o.tile_bits : default_tile_bits(prec), M);
-        std::vector<TileOp<float2>> ops;
-        std::vector<unsigned char> runs;
-        std::vector<int> all(scratch.gates.size());
-        for (size_t i = 0; i < all.size(); ++i) all[i] = int(i);
-        plan_tiled(&scratch, b, all, ops, runs);
-        std::vector<RegOp> regops;
-        std::vector<RoundDesc> rounds;
-        for (Step &st : scratch.steps) {
-            if (st.type != S_TILE) continue;
-            const int RB = st.d.b - kRegThreadBits;
-            if (RB < 3 || RB > 4) continue;
-            TilePassDesc d = st.d;
-            if (build_rounds(ops, st.d.op_begin, st.d.op_count, d, RB, regops, rounds, runs)) st.d = d;
+    if (o.subspace) {
+        if (int rc = plan_subspace(p)) {
+            plan_release(p);
+            return rc;
         }
-        const double t_tiled = model_seconds(&scratch, regops);
-        const double t_fused = double(count_fused_blocks(p->gates, 5)) * 16.0 * std::ldexp(1.0, M) / kModelFusedBw;
-        if (t_fused < t_tiled) mode = QSIM_MODE_FUSED;
+        *out = p;
+        return QSIM_OK;
+    }
+    int mode = o.mode == QSIM_MODE_AUTO ? QSIM_MODE_TILED : o.mode;
+    int auto_b = 0, auto_k = 0;
+    if (o.mode == QSIM_MODE_AUTO && prec == QSIM_C64 && M >= 20) {
+        // the candidates (tile passes of 2^12 or 2^11 amplitudes, fused blocks
+        // of width 5, 4 or 3, unless opts fix them) planned on the host and
+        // timed by the model with the device's measured rates
+        ModelRates rates{};
+        std::string src;
+        if (int rc = model_rates(prec, o.specialize != 0 && jit_available(), &rates, &src)) {
+            plan_release(p);
+            return rc;
+        }
+        std::string log = "auto:";
+        double best = 1e300;
         char line[160];
-        std::snprintf(line, sizeof line, "auto: tiled %.3g s, fused %.3g s (model)", t_tiled, t_fused);
-        p->auto_log = line;
+        for (int b : {12, 11}) {
+            if (o.tile_bits && b != o.tile_bits) continue;
+            if (b > M) continue;
+            qsim_plan scratch;
+            scratch.M = M;
+            scratch.prec = prec;
+            scratch.gates = p->gates;
+            split_row_phases(scratch.gates);
+            std::vector<TileOp<float2>> ops;
+            std::vector<unsigned char> runs;
+            std::vector<int> all(scratch.gates.size());
+            for (size_t i = 0; i < all.size(); ++i) all[i] = int(i);
+            plan_tiled(&scratch, b, all, ops, runs);
+            std::vector<RegOp> regops;
+            std::vector<RoundDesc> rounds;
+            for (Step &st : scratch.steps) {
+                if (st.type != S_TILE) continue;
+                const int RB = st.d.b - kRegThreadBits;
+                if (RB < 3 || RB > 4) continue;
+                TilePassDesc d = st.d;
+                if (build_rounds(ops, st.d.op_begin, st.d.op_count, d, RB, regops, rounds, runs)) st.d = d;
+            }
+            const double t = model_seconds(&scratch, regops, rates);
+            std::snprintf(line, sizeof line, " tiled b=%d %.3g s (%zu passes),", b, t, scratch.steps.size());
+            log += line;
+            if (t < best) {
+                best = t;
+                mode = QSIM_MODE_TILED;
+                auto_b = b;
+                auto_k = 0;
+            }
+        }
+        for (int k : {5, 4, 3}) {
+            if (o.fuse_k && k != std::max(3, o.fuse_k)) continue;
+            int nb = 0;
+            const double t = model_fused(p->gates, k, M, rates, &nb);
+            std::snprintf(line, sizeof line, " fused k=%d %.3g s (%d blocks),", k, t, nb);
+            log += line;
+            if (t < best) {
+                best = t;
+                mode = QSIM_MODE_FUSED;
+                auto_k = k;
+                auto_b = 0;
+            }
+        }
+        std::snprintf(line, sizeof line, " chosen %s %d; rates %s", mode == QSIM_MODE_FUSED ? "fused k=" : "tiled b=",
+                      mode == QSIM_MODE_FUSED ? auto_k : auto_b, src.c_str());
+        log += line;
+        p->auto_log = log;
     }
     // The tensor-core kernel runs 4- or 5-qubit blocks of complex64 states
     // with at least 2^(k+7) amplitudes; anything else takes the tile passes.
-    const int k_eff = o.fuse_k == 0 ? 5 : std::max(3, o.fuse_k);
+    const int k_eff = auto_k ? auto_k : o.fuse_k == 0 ? 5 : std::max(3, o.fuse_k);
     if (mode == QSIM_MODE_FUSED && (prec != QSIM_C64 || M < kFusedTileBits)) mode = QSIM_MODE_TILED;
     p->mode = mode;
     {
@@ -1488,7 +1788,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
             p->steps.push_back(st);
         }
     } else {
-        const int b = o.tile_bits ? o.tile_bits : default_tile_bits(prec);
+        const int b = auto_b ? auto_b : o.tile_bits ? o.tile_bits : default_tile_bits(prec);
         p->tile_bits = std::min(b, M);
         int rc = tile_prepare(prec);
         if (rc == QSIM_OK && prec == QSIM_C64) rc = tile_reg_prepare();
@@ -1621,6 +1921,8 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
 
 void plan_release(qsim_plan *p) {
     if (!p) return;
+    for (qsim_plan *c : p->seg_plans) plan_release(c);
+    if (p->relabel) plan_release(p->relabel);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     dev_free(p, p->d_ops, p->ops_bytes);
@@ -1650,6 +1952,7 @@ int qsim_plan_execute(const qsim_plan *p, qsim_state *dst, const qsim_state *src
         set_error("state (M=%d) does not match the plan (M=%d)", dst->M, p->M);
         return QSIM_EINVAL;
     }
+    if (p->subspace) return run_subspace(p, dst);  // the input is |0...0>: src is not read
     cudaStream_t s = dst->stream;
     if (src != dst && src->stream != s) {
         QS_CUDA(cudaEventRecord(src->ev, src->stream));
@@ -1731,6 +2034,20 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
     };
     static const char *kinds[] = {"DENSE", "RDENSE", "SWAP"};
     add("M=%d prec=%s mode=%d steps=%zu\n", p->M, p->prec == QSIM_C64 ? "c64" : "c128", p->mode, p->steps.size());
+    if (p->subspace) {
+        add("subspace: %zu segments, %lld gates left out (control never touched), %zu qubits touched, "
+            "amp-updates %.6g of %.6g flat, relabel passes %lld\n",
+            p->seg_plans.size(), (long long)p->sub_skipped, p->sub_order.size(), p->sub_amp_updates,
+            p->stats.amp_updates, p->relabel ? (long long)p->relabel->steps.size() : 0LL);
+        add("touch order:");
+        for (int q : p->sub_order) add(" %d", q);
+        add("\n");
+        for (size_t i = 0; i < p->seg_plans.size(); ++i) {
+            const qsim_plan *c = p->seg_plans[i];
+            add("segment %zu M=%d gates=%lld mode=%d passes=%lld\n", i, p->seg_M[i], (long long)c->stats.n_gates,
+                c->stats.mode, (long long)c->stats.n_passes);
+        }
+    }
     if (!p->jit_log.empty()) add("specialisation: %s\n", p->jit_log.c_str());
     if (!p->auto_log.empty()) add("%s\n", p->auto_log.c_str());
     for (size_t j = 0; j < p->steps.size(); ++j) {

@@ -42,6 +42,21 @@ DevAllocator current_allocator();
 int dmalloc(const DevAllocator &a, void **p, size_t bytes, cudaStream_t s, const char *what);
 void dfree(const DevAllocator &a, void *p, size_t bytes, cudaStream_t s);
 
+// ------------------------------------------------------------- autotuning
+// Rates of the execution forms measured on the device (tune.cu), in bytes/s
+// (read + write) or FMA-equivalents/s; fused rates per block width k, for
+// blocks off qubits 0..4 (direct stores) and on them (staged stores).
+struct ModelRates {
+    double pass_bw, fma_rate, perm_bw;
+    double fused_direct[6], fused_staged[6];
+};
+int model_rates(qsim_prec prec, bool specialised, ModelRates *r, std::string *source);
+// A persisted value under `key` in the tuning cache (1 if found).
+int tune_lookup(const std::string &key, double *value);
+void tune_record(const std::string &key, double value);
+std::string tune_device_key();
+double plan_model_fma(const ::qsim_plan *p);  // FMA-equivalents per amplitude over the plan's tile passes
+
 // ------------------------------------------------------------------- gates
 // Gate kinds, chosen from the matrix on the host:
 //   DENSE  : general 2x2
@@ -220,6 +235,7 @@ int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector
               const std::vector<RegOp> &regops, const std::vector<RoundDesc> &rounds,
               const std::vector<unsigned char> &runs, std::vector<cudaLibrary_t> *libs,
               std::vector<cudaKernel_t> *kernels, std::string *log);
+bool jit_available();  // NVRTC could be loaded
 void jit_release(cudaLibrary_t lib);
 void jit_release(const std::vector<cudaLibrary_t> &libs);
 // The persistent trajectory kernel in register rounds ("qs_traj"): passes with

@@ -504,6 +504,23 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) best = it->second;
     }
+    // the persisted choice for this circuit on this device (FNV-1a of the key)
+    uint64_t h = 1469598103934665603ull;
+    for (double x : key) {
+        unsigned char b[sizeof x];
+        std::memcpy(b, &x, sizeof x);
+        for (unsigned char c : b) h = (h ^ c) * 1099511628211ull;
+    }
+    char hkey[64];
+    snprintf(hkey, sizeof hkey, "%016llx", (unsigned long long)h);
+    const std::string file_key = "traj|" + tune_device_key() + "|" + hkey;
+    if (best == 0) {
+        double v = 0;
+        if (tune_lookup(file_key, &v) && v >= 10) {
+            best = int(v);
+            p->tune += "configuration replayed from the tuning cache\n";
+        }
+    }
     if (best == 0) {
         std::vector<int> cands;
         if (o.kernel != 2)
@@ -558,6 +575,9 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
         cudaEventDestroy(e1);
         if (rc) return fail(rc);
         if (best == 0) best = 10;
+        tune_record(file_key, double(best));
+    }
+    {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = best;
     }

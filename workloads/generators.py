@@ -331,3 +331,56 @@ def request_circuit(req):
     """Circuit of one served request (drawn as the random circuit above)."""
     return circuit_c1_random(req["M"], req["n_gates"], req["sigma"],
                              seed_circuit=list(req["seed_circuit"]), seed_err=list(req["seed_err"]))
+
+
+def circuit_gradual(M: int, start: int = 4, per_qubit: int = 16, sigma: float = 1e-3, order=None,
+                    seed_circuit=0, seed_err=1):
+    """A circuit that touches its qubits one at a time, as the modular
+    arithmetic of the paper's factoring circuits reaches its work registers
+    late (Section 3.2, Figure 7): Hadamards on the first ``start`` qubits of
+    ``order`` (default 0, 1, ..., M-1); then for each further qubit q of
+    ``order`` a CNOT from a random touched qubit onto q, followed by
+    ``per_qubit`` gates drawn among: a Haar SU(2) on a touched qubit, a
+    controlled phase between touched qubits, a Toffoli on touched qubits, a
+    CNOT controlled by a qubit not touched yet (the identity at that point),
+    and an Rz on a qubit not touched yet (a phase on its 0 component).  Every
+    gate carries a Gaussian over-rotation error (sigma) about its own axis
+    (x for the X-type gates, z for the diagonal ones)."""
+    rng = np.random.default_rng(seed_circuit)
+    order = list(range(M)) if order is None else [int(q) for q in order]
+    assert sorted(order) == list(range(M)) and 1 <= start <= M
+    recs, axes = [], []
+
+    def add(U, t, ctl=(), ax=(0.0, 0.0, 1.0)):
+        recs.append(gate_record(U, t, ctl))
+        axes.append(ax)
+
+    for q in order[:start]:
+        add(mat_h(), q, (), (1.0 / np.sqrt(2.0), 0.0, 1.0 / np.sqrt(2.0)))
+    touched = list(order[:start])
+    for q in order[start:]:
+        add(mat_x(), q, (int(rng.choice(touched)),), (1.0, 0.0, 0.0))
+        touched.append(q)
+        rest = [v for v in order if v not in touched]
+        for _ in range(per_qubit):
+            r = rng.random()
+            if r < 0.45:
+                U = mat_haar_su2(rng)
+                add(U, int(rng.choice(touched)), (), su2_axis(U)[1])
+            elif r < 0.75 and len(touched) >= 2:
+                a, b = (int(v) for v in rng.choice(touched, size=2, replace=False))
+                add(mat_phase(float(rng.uniform(0, 2 * np.pi))), a, (b,))
+            elif r < 0.85 and len(touched) >= 3:
+                a, b, c = (int(v) for v in rng.choice(touched, size=3, replace=False))
+                add(mat_x(), a, (b, c), (1.0, 0.0, 0.0))
+            elif r < 0.93 and rest:
+                add(mat_x(), int(rng.choice(touched)), (int(rng.choice(rest)),), (1.0, 0.0, 0.0))
+            elif rest:
+                add(mat_rz(float(rng.uniform(0, 2 * np.pi))), int(rng.choice(rest)))
+            else:
+                U = mat_haar_su2(rng)
+                add(U, int(rng.choice(touched)), (), su2_axis(U)[1])
+    ideal = _pack(recs)
+    ax = np.array(axes, dtype=np.float64)
+    eps = np.random.default_rng(seed_err).normal(0.0, sigma, size=len(recs))
+    return {"M": M, "ideal": ideal, "axes": ax, "eps": eps, "noisy": with_errors(ideal, ax, eps)}
