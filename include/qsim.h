@@ -253,6 +253,13 @@ int qsim_plan_timing(qsim_plan *plan, int64_t n_max, double *ms, double *bytes, 
 int qsim_fidelity(const qsim_state *ideal, const qsim_state *noisy,
                   double *F, double *norm_noisy);
 
+/* The sums behind qsim_fidelity: out[0] = sum_i |noisy_i|^2, out[1] + i out[2]
+ * = sum_i conj(ideal_i) noisy_i, same order and accumulation.  For a state
+ * split over ranks (qsim_shard_plan_create) each rank's three sums add up to
+ * the whole state's (an all-reduce of 3 doubles; EQ 3's global sum); then
+ * F = out[1]^2 + out[2]^2.  Waits for noisy's stream. */
+int qsim_overlap(const qsim_state *ideal, const qsim_state *noisy, double out[3]);
+
 /* norm = sum_i |a_i|^2 (Section 1.2), FP64 accumulation. */
 int qsim_norm(const qsim_state *st, double *norm);
 
@@ -420,6 +427,51 @@ void qsim_server_destroy(qsim_server *srv);
 typedef void *(*qsim_device_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx);
 typedef void (*qsim_device_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *ctx);
 int qsim_set_allocator(qsim_device_alloc_fn alloc, qsim_device_free_fn free, void *ctx);
+
+/* ------------------------------------------------------------- sharding */
+
+/* One state over P = 2^n_global ranks (Section 3.1; Section 3.3, Figure 8):
+ * the values of n_global qubits (initially the top ones, M - n_global ..
+ * M - 1) select the rank that holds an amplitude; each rank holds the
+ * 2^L amplitudes (L = M - n_global) of its rank bits as an L-qubit state,
+ * local qubit s = bit s of the local index.  The plan (host records only, no
+ * device work) lists, for one rank, the steps that apply the circuit:
+ *   kind 0: gates on the local state (qsim_shard_step_gates; run them with a
+ *           plan of L qubits).  A gate controlled by a rank bit that is 0 on
+ *           this rank is left out, a control on a rank bit that is 1 is
+ *           dropped, and a diagonal gate on a rank-bit target becomes the
+ *           factor of this rank's bit;
+ *   kind 1: a redistribution of n_pairs qubits (global_bits[i] = the rank bit
+ *           j_i of pair i): with C = 2^(L - n_pairs) and the local state cut
+ *           into chunks of C amplitudes (chunk b = the values of the top
+ *           n_pairs local bits, bit i of b for pair i), this rank exchanges,
+ *           for every b other than its own bits (rank >> j_i) & 1, its chunk b
+ *           with the same-sized chunk of the rank whose bits j_i equal b and
+ *           whose other bits equal this rank's (the partner's chunk b' = this
+ *           rank's own index): send chunk b, receive into chunk b.  Afterwards
+ *           the top local qubit L - n_pairs + i and rank bit j_i have traded
+ *           their logical qubits.
+ * A redistribution is planned only when a non-diagonal gate targets a qubit
+ * held in a rank bit: that qubit trades places with the local qubit whose next
+ * use as such a target lies furthest ahead (the same choice on every rank).
+ * With restore_order != 0 the plan ends in the starting layout (logical
+ * qubit q at local bit q, or at rank bit q - L).  Rank in [0, 2^n_global),
+ * n_global in [0, min(M - 1, 20)]. */
+typedef struct qsim_shard_plan qsim_shard_plan;
+int qsim_shard_plan_create(int M, int n_global, int rank, const qsim_gate *gates, size_t n, int restore_order,
+                           qsim_shard_plan **out);
+/* Steps, redistributions, and the sum over redistributions of the fraction
+ * of a shard each rank sends (1 - 2^-n_pairs each; EQ 2's reorganised blocks
+ * over all blocks).  Any output may be NULL. */
+int qsim_shard_plan_info(const qsim_shard_plan *p, int64_t *n_steps, int64_t *n_exchanges, double *moved);
+/* Step i: kind (0 local gates, 1 redistribution), its gate count, its pair
+ * count and the rank bits of the pairs (global_bits: room for n_global ints;
+ * may be NULL).  Any output may be NULL. */
+int qsim_shard_step(const qsim_shard_plan *p, int64_t i, int *kind, int64_t *n_gates, int *n_pairs,
+                    int *global_bits);
+/* The local gates of step i (qubits numbered 0 .. L-1) into out[0 .. n_gates). */
+int qsim_shard_step_gates(const qsim_shard_plan *p, int64_t i, qsim_gate *out, size_t cap);
+void qsim_shard_plan_destroy(qsim_shard_plan *p);
 
 /* ----------------------------------------------------------- autotuning */
 

@@ -115,6 +115,7 @@ SIGNATURES = [
     ("qsim_plan_timing", ctypes.c_int, [_vp, ctypes.c_int64, _dp, _dp, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int64)]),
     ("qsim_fidelity", ctypes.c_int, [_vp, _vp, _dp, _dp]),
+    ("qsim_overlap", ctypes.c_int, [_vp, _vp, _dp]),
     ("qsim_norm", ctypes.c_int, [_vp, _dp]),
     ("qsim_probabilities", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     ("qsim_fidelity_noalloc", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
@@ -133,6 +134,13 @@ SIGNATURES = [
     ("qsim_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
     ("qsim_server_destroy", None, [_vp]),
     ("qsim_set_allocator", ctypes.c_int, [_vp, _vp, _vp]),
+    ("qsim_shard_plan_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t,
+                                              ctypes.c_int, ctypes.POINTER(_vp)]),
+    ("qsim_shard_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                            _dp]),
+    ("qsim_shard_step", ctypes.c_int, [_vp, ctypes.c_int64, _ip, ctypes.POINTER(ctypes.c_int64), _ip, _ip]),
+    ("qsim_shard_step_gates", ctypes.c_int, [_vp, ctypes.c_int64, _vp, ctypes.c_size_t]),
+    ("qsim_shard_plan_destroy", None, [_vp]),
     ("qsim_tune_set_cache", ctypes.c_int, [ctypes.c_char_p]),
     ("qsim_tune_rates", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int64,
                                        ctypes.POINTER(ctypes.c_int64)]),

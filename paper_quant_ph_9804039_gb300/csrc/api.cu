@@ -229,6 +229,27 @@ int qsim_apply_gate(qsim_state *st, const double U[8], int target, const int *co
     return launch_gate(st->amps, st->M, st->prec, g, st->stream);
 }
 
+int qsim_overlap(const qsim_state *ideal, const qsim_state *noisy, double out[3]) {
+    if (!out) { set_error("out is NULL"); return QSIM_EINVAL; }
+    if (int rc = check_state(ideal)) return rc;
+    if (int rc = check_state(noisy)) return rc;
+    if (ideal->M != noisy->M || ideal->prec != noisy->prec) {
+        set_error("states differ in M or precision");
+        return QSIM_EINVAL;
+    }
+    if (ideal->stream != noisy->stream) {
+        QS_CUDA(cudaEventRecord(ideal->ev, ideal->stream));
+        QS_CUDA(cudaStreamWaitEvent(noisy->stream, ideal->ev, 0));
+    }
+    if (int rc = launch_reduce(ideal->amps, noisy->amps, noisy->M, noisy->prec, noisy->scratch,
+                               noisy->scratch_blocks, noisy->stream))
+        return rc;
+    QS_CUDA(cudaMemcpyAsync(out, noisy->scratch + 3 * size_t(noisy->scratch_blocks), 3 * sizeof(double),
+                            cudaMemcpyDeviceToHost, noisy->stream));
+    QS_CUDA(cudaStreamSynchronize(noisy->stream));
+    return QSIM_OK;
+}
+
 int qsim_fidelity(const qsim_state *ideal, const qsim_state *noisy, double *F, double *norm_noisy) {
     if (int rc = check_state(ideal)) return rc;
     if (int rc = check_state(noisy)) return rc;
