@@ -57,6 +57,9 @@ def _declare(lib):
     lib.orc_trajectories.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ip, ip, ip, dp, dp,
                                      ctypes.c_int, dp, dp, dp, ctypes.c_int]
     lib.orc_trajectories.restype = ctypes.c_int
+    lib.orc_decoherence.argtypes = [dp, ctypes.c_int, ctypes.c_int64, dp, ip, ip, ip, dp, dp, ctypes.c_double, ip,
+                                    dp, ctypes.c_int]
+    lib.orc_decoherence.restype = ctypes.c_int
     return lib
 
 
@@ -176,6 +179,23 @@ class Oracle:
         if rc:
             raise ValueError("oracle rejected the trajectory batch")
         return F, float(mean[0]), float(var[0])
+
+    def decoherence(self, psi: np.ndarray, recs, delta, r, gamma: float, nthreads: int = 1):
+        """Gates with dephasing and amplitude-damping jumps after each one, in
+        place; returns (jumps[n], p[n])."""
+        assert psi.dtype == np.complex128 and psi.flags.c_contiguous
+        M = int(psi.size).bit_length() - 1
+        U, t, nc, c = _arrays(recs)
+        delta = np.ascontiguousarray(delta, dtype=np.float64)
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        assert delta.size == len(t) and r.size == len(t)
+        jumps = np.zeros(len(t), dtype=np.int32)
+        p = np.zeros(len(t))
+        rc = self.lib.orc_decoherence(_dp(psi.view(np.float64)), M, len(t), _dp(U), _ip(t), _ip(nc), _ip(c),
+                                      _dp(delta), _dp(r), float(gamma), _ip(jumps), _dp(p), int(nthreads))
+        if rc:
+            raise ValueError("oracle rejected the decoherence run")
+        return jumps, p
 
     # whole runs ------------------------------------------------------------
     def run(self, M: int, recs, psi0=None, nthreads: int = 1) -> np.ndarray:

@@ -250,3 +250,63 @@ int orc_trajectories(int M, int64_t n, const double *U, const int *target, const
     free(ideal);
     return 0;
 }
+
+/* ------------------------------------------------------------ decoherence */
+
+/* Weights of the qubit's 1 states and of all states: P1 = sum over i with
+ * bit t set of |psi_i|^2, N = sum_i |psi_i|^2. */
+static void weights(const cplx *psi, int M, int t, double *P1, double *N)
+{
+    const uint64_t n = (uint64_t)1 << M, tb = (uint64_t)1 << t;
+    double p1 = 0.0, all = 0.0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const double w = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
+        all += w;
+        if (i & tb) p1 += w;
+    }
+    *P1 = p1;
+    *N = all;
+}
+
+/* Decoherence after every operation (Section 3.4: two more transformations
+ * after each operation and a sum over the whole state; EQ 3, EQ 8).  The
+ * paper does not give the transformations; the reading taken here: after
+ * gate g on target t,
+ *   1. dephasing: Rz(delta_g) = diag(e^{-i delta/2}, e^{+i delta/2}) on t;
+ *   2. amplitude damping as a quantum jump on t: with P1 and N the weights
+ *      above, p = gamma P1 / N is the jump probability; if r_g < p the jump
+ *      operator [[0, sqrt(gamma)], [0, 0]] is applied, else the no-jump
+ *      operator diag(1, sqrt(1 - gamma)), each scaled so that the norm stays
+ *      N: by sqrt(N / (gamma P1)), or sqrt(N / (N - gamma P1)).
+ * delta and r come from the caller (seeded); jumps[g] and p_out[g] (may be
+ * NULL) receive the decision and p. */
+int orc_decoherence(double *psi_ri, int M, int64_t n, const double *U, const int *target, const int *nctl,
+                    const int *ctl, const double *delta, const double *r, double gamma, int *jumps,
+                    double *p_out, int nthreads)
+{
+    if (gamma < 0.0 || gamma > 1.0) return -1;
+    cplx *psi = (cplx *)psi_ri;
+    for (int64_t g = 0; g < n; ++g) {
+        const int t = target[g];
+        if (orc_apply_gate(psi_ri, M, U + 8 * g, t, ctl + 2 * g, nctl[g], nthreads)) return -1;
+        const double h = 0.5 * delta[g];
+        const double Rz[8] = {cos(h), -sin(h), 0, 0, 0, 0, cos(h), sin(h)};
+        orc_apply_gate(psi_ri, M, Rz, t, NULL, 0, nthreads);
+        double P1, N;
+        weights(psi, M, t, &P1, &N);
+        const double p = N > 0.0 ? gamma * P1 / N : 0.0;
+        const int jump = r[g] < p;
+        double K[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (jump) {
+            K[2] = sqrt(gamma) * sqrt(N / (gamma * P1));
+        } else {
+            const double s = sqrt(N / (N - gamma * P1));
+            K[0] = s;
+            K[6] = sqrt(1.0 - gamma) * s;
+        }
+        orc_apply_gate(psi_ri, M, K, t, NULL, 0, nthreads);
+        if (jumps) jumps[g] = jump;
+        if (p_out) p_out[g] = p;
+    }
+    return 0;
+}

@@ -260,4 +260,91 @@ def pin_trajectory_statistics(orc):
         assert abs(orc.fidelity(ideal, noisy)[0] - F[t]) < 1e-12
 
 
+def _decoherence_brute(M, recs, delta, r, gamma, psi):
+    """The decoherence reading written out with 2^M x 2^M matrices and numpy
+    sums: gate, Rz(delta) on the target, then the jump (r < gamma P1 / N) or
+    no-jump operator scaled to keep the norm."""
+    psi = psi.astype(np.complex128).copy()
+    jumps = []
+    for g in range(len(recs)):
+        t = int(recs[g]["target"])
+        ctl = tuple(int(c) for c in recs[g]["controls"][: int(recs[g]["ncontrols"])])
+        psi = dense_gate(M, W.record_matrix(recs[g]), t, ctl) @ psi
+        psi = dense_gate(M, W.mat_rz(delta[g]), t) @ psi
+        ones = (np.arange(1 << M) >> t) & 1 == 1
+        P1 = float(np.sum(np.abs(psi[ones]) ** 2))
+        N = float(np.sum(np.abs(psi) ** 2))
+        p = gamma * P1 / N
+        if r[g] < p:
+            K = np.array([[0, np.sqrt(gamma)], [0, 0]]) * np.sqrt(N / (gamma * P1))
+        else:
+            K = np.diag([1.0, np.sqrt(1 - gamma)]) * np.sqrt(N / (N - gamma * P1))
+        psi = dense_gate(M, K, t) @ psi
+        jumps.append(int(r[g] < p))
+    return psi, np.array(jumps)
+
+
+def pin_decoherence_brute_force(orc):
+    """Decoherence (Section 3.4 reading): the oracle's run equals the same
+    steps written with dense matrices, for random circuits and jump draws."""
+    rng = np.random.default_rng(17)
+    for M in (1, 3, 4):
+        recs = W._pack([W.gate_record(*_rand_gate(rng, M)) for _ in range(10)])
+        delta = rng.normal(0, 0.3, len(recs))
+        r = rng.random(len(recs)) * 0.6
+        psi0 = _rand_state(rng, M)
+        ref, jref = _decoherence_brute(M, recs, delta, r, 0.4, psi0)
+        got = psi0.astype(np.complex128).copy()
+        jumps, p = orc.decoherence(got, recs, delta, r, 0.4)
+        assert np.array_equal(jumps, jref)
+        assert np.allclose(got, ref, atol=1e-12, rtol=0)
+        assert abs(orc.norm(got) - orc.norm(psi0)) < 1e-12
+
+
+def pin_decoherence_single_qubit(orc):
+    """Closed forms on one qubit: X from |0> then damping gives |0> after a
+    jump (r < gamma) and |1> after none; H gives p = gamma / 2 and, without a
+    jump, (1, sqrt(1 - gamma)) / sqrt(2 - gamma); gamma = 0 with delta only is
+    H then Rz(delta)."""
+    g = 0.3
+    for r, want in ((0.1, [1, 0]), (0.5, [0, 1])):
+        psi = orc.zero_state(1)
+        jumps, p = orc.decoherence(psi, W._pack([W.gate_record(W.mat_x(), 0)]), [0.0], [r], g)
+        assert abs(p[0] - g) < 1e-15 and jumps[0] == int(r < g)
+        assert np.allclose(psi, want, atol=1e-15)
+    psi = orc.zero_state(1)
+    jumps, p = orc.decoherence(psi, W._pack([W.gate_record(W.mat_h(), 0)]), [0.0], [0.9], g)
+    assert abs(p[0] - g / 2) < 1e-15 and jumps[0] == 0
+    assert np.allclose(psi, np.array([1.0, np.sqrt(1 - g)]) / np.sqrt(2 - g), atol=1e-15)
+    psi = orc.zero_state(1)
+    orc.decoherence(psi, W._pack([W.gate_record(W.mat_h(), 0)]), [0.8], [0.9], 0.0)
+    assert np.allclose(psi, np.array([np.exp(-0.4j), np.exp(0.4j)]) / np.sqrt(2), atol=1e-15)
+
+
+def pin_decoherence_channel(orc):
+    """The two branches weighted by their probabilities give the amplitude-
+    damping channel: p rho_jump + (1 - p) rho_nojump = K0 rho K0^+ + K1 rho K1^+
+    (for a random 3-qubit state and each target), and gamma = delta = 0 is the
+    plain circuit, bit for bit."""
+    rng = np.random.default_rng(5)
+    M, g = 3, 0.35
+    psi0 = _rand_state(rng, M)
+    rho = np.outer(psi0, psi0.conj())
+    for t in range(M):
+        ident = W._pack([W.gate_record(np.eye(2), t)])
+        a = psi0.copy()
+        ja, p = orc.decoherence(a, ident, [0.0], [0.0], g)
+        b = psi0.copy()
+        jb, _ = orc.decoherence(b, ident, [0.0], [1.0], g)
+        assert ja[0] == 1 and jb[0] == 0
+        mix = p[0] * np.outer(a, a.conj()) + (1 - p[0]) * np.outer(b, b.conj())
+        K0 = dense_gate(M, np.diag([1.0, np.sqrt(1 - g)]), t)
+        K1 = dense_gate(M, np.array([[0, np.sqrt(g)], [0, 0]]), t)
+        assert np.allclose(mix, K0 @ rho @ K0.conj().T + K1 @ rho @ K1.conj().T, atol=1e-13)
+    recs = W._pack([W.gate_record(*_rand_gate(rng, M)) for _ in range(8)])
+    c = psi0.copy()
+    orc.decoherence(c, recs, np.zeros(len(recs)), np.full(len(recs), 0.5), 0.0)
+    assert np.array_equal(c, orc.run(M, recs, psi0))
+
+
 PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

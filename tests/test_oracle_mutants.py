@@ -37,6 +37,13 @@ MUTANTS = {
     "variance_biased": [("*var = (T > 1) ? v / (T - 1) : 0.0;", "*var = v / T;")],
     "probability_amplitude": [("p[i] = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);",
                                "p[i] = creal(psi[i]) + cimag(psi[i]);")],
+    "decoherence_branch_flipped": [("const int jump = r[g] < p;", "const int jump = r[g] >= p;")],
+    "decoherence_p1_on_zero_states": [("if (i & tb) p1 += w;", "if (!(i & tb)) p1 += w;")],
+    "decoherence_no_renormalisation": [("const double s = sqrt(N / (N - gamma * P1));", "const double s = 1.0;")],
+    "decoherence_dephasing_sign": [("const double Rz[8] = {cos(h), -sin(h), 0, 0, 0, 0, cos(h), sin(h)};",
+                                    "const double Rz[8] = {cos(h), sin(h), 0, 0, 0, 0, cos(h), -sin(h)};")],
+    "decoherence_jump_on_zero": [("K[2] = sqrt(gamma) * sqrt(N / (gamma * P1));",
+                                  "K[4] = sqrt(gamma) * sqrt(N / (gamma * P1));")],
 }
 
 
