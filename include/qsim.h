@@ -428,6 +428,31 @@ typedef void *(*qsim_device_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx
 typedef void (*qsim_device_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *ctx);
 int qsim_set_allocator(qsim_device_alloc_fn alloc, qsim_device_free_fn free, void *ctx);
 
+/* ---------------------------------------------------------- decoherence */
+
+/* A circuit with decoherence after every operation (Section 3.4: two more
+ * transformations after each operation and a sum over the whole state; EQ 3,
+ * EQ 8).  The paper leaves the transformations open; this library's reading:
+ * after gate g on target t (applied where its controls are 1),
+ *   1. dephasing: Rz(delta[g]) = diag(e^{-i delta/2}, e^{+i delta/2}) on t
+ *      (on every amplitude);
+ *   2. amplitude damping on t as a quantum jump: with P1 = the summed |a|^2
+ *      of t's 1 states and N = the norm, p = gamma P1 / N; if r[g] < p the
+ *      jump operator [[0, sqrt(gamma)], [0, 0]] is applied, otherwise the
+ *      no-jump operator diag(1, sqrt(1 - gamma)), each scaled so that the
+ *      norm stays N.
+ * The state is updated in place on its stream; delta (radians) and r
+ * (uniform draws in [0, 1)) are n doubles each, chosen by the caller (seeded),
+ * so runs are reproducible.  jumps[g] (n int32, may be NULL) receives 1 where
+ * the jump was taken and p_out[g] (n doubles, may be NULL) the probability p;
+ * the sums are FP64 and in a fixed order.  One pass over the state per
+ * operation: the damping of operation g is applied in the pass of gate g + 1.
+ * gamma in [0, 1]; QSIM_EINVAL for a bad gate or a non-finite delta or r.
+ * Allocates 32 KiB + 12 n bytes of device scratch for the call.  Waits for
+ * the state's stream. */
+int qsim_run_decoherence(qsim_state *st, const qsim_gate *gates, size_t n, const double *delta, const double *r,
+                         double gamma, int32_t *jumps, double *p_out);
+
 /* ------------------------------------------------------------- sharding */
 
 /* One state over P = 2^n_global ranks (Section 3.1; Section 3.3, Figure 8):

@@ -134,6 +134,8 @@ SIGNATURES = [
     ("qsim_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
     ("qsim_server_destroy", None, [_vp]),
     ("qsim_set_allocator", ctypes.c_int, [_vp, _vp, _vp]),
+    ("qsim_run_decoherence", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _dp, _dp, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int32), _dp]),
     ("qsim_shard_plan_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t,
                                               ctypes.c_int, ctypes.POINTER(_vp)]),
     ("qsim_shard_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -500,6 +502,21 @@ def run_trajectories(M: int, gates, err_axis, eps, fuse_k: int = 0, use_graph: b
 
 def version() -> str:
     return load_library().qsim_version().decode()
+
+
+def run_decoherence(state: State, gates, delta, r, gamma: float):
+    """qsim_run_decoherence on `state` in place: returns (jumps[n], p[n])."""
+    lib = load_library()
+    g = _records(gates)
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    assert d.size == len(g) and rr.size == len(g)
+    jumps = np.zeros(len(g), dtype=np.int32)
+    p = np.zeros(len(g))
+    _check(lib.qsim_run_decoherence(state.handle, _vp(g.ctypes.data), len(g), d.ctypes.data_as(_dp),
+                                    rr.ctypes.data_as(_dp), float(gamma),
+                                    jumps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), p.ctypes.data_as(_dp)))
+    return jumps, p
 
 
 # qsim_device_alloc_fn / qsim_device_free_fn of include/qsim.h
