@@ -60,6 +60,8 @@ def _declare(lib):
     lib.orc_decoherence.argtypes = [dp, ctypes.c_int, ctypes.c_int64, dp, ip, ip, ip, dp, dp, ctypes.c_double, ip,
                                     dp, ctypes.c_int]
     lib.orc_decoherence.restype = ctypes.c_int
+    lib.orc_qutrit_apply.argtypes = [dp, ctypes.c_int, ctypes.c_int64, dp, ip, ip, ip, ip]
+    lib.orc_qutrit_apply.restype = ctypes.c_int
     return lib
 
 
@@ -196,6 +198,20 @@ class Oracle:
         if rc:
             raise ValueError("oracle rejected the decoherence run")
         return jumps, p
+
+    def qutrit_apply(self, psi: np.ndarray, recs3):
+        """Three-level transformation records applied in order to 3^M
+        amplitudes, in place."""
+        from workloads.generators import records3_to_arrays
+        assert psi.dtype == np.complex128 and psi.flags.c_contiguous
+        M = round(np.log(psi.size) / np.log(3))
+        assert 3 ** M == psi.size
+        U, t, nc, c, lv = records3_to_arrays(recs3)
+        rc = self.lib.orc_qutrit_apply(_dp(psi.view(np.float64)), M, len(t), _dp(U), _ip(t), _ip(nc), _ip(c),
+                                       _ip(lv))
+        if rc:
+            raise ValueError("oracle rejected a qutrit transformation")
+        return psi
 
     # whole runs ------------------------------------------------------------
     def run(self, M: int, recs, psi0=None, nthreads: int = 1) -> np.ndarray:

@@ -310,3 +310,46 @@ int orc_decoherence(double *psi_ri, int M, int64_t n, const double *U, const int
     }
     return 0;
 }
+
+/* ----------------------------------------------------------------- qutrits */
+
+/* The three-state model (Section 2.0, Section 3.0-3.1): M three-level
+ * particles, 3^M complex amplitudes, the index written in base 3 with digit q
+ * the level of particle q (digit 0 least significant).  A transformation on
+ * one particle is a 3x3 matrix U applied to every triple of states that
+ * differ only in that particle's level: (a_i, a_{i + 3^t}, a_{i + 2 3^t}) for
+ * every i whose digit t is 0.  A control (c, v) restricts it to the triples
+ * whose digit c equals v.  U is row-major, re/im interleaved (18 doubles). */
+int orc_qutrit_apply(double *psi_ri, int M, int64_t n, const double *U /* [n][18] */, const int *target,
+                     const int *nctl, const int *ctl /* [n][2] */, const int *lvl /* [n][2] */)
+{
+    if (M < 1 || M > 24) return -1;
+    cplx *psi = (cplx *)psi_ri;
+    uint64_t pw[26];
+    pw[0] = 1;
+    for (int q = 1; q <= M; ++q) pw[q] = pw[q - 1] * 3;
+    for (int64_t g = 0; g < n; ++g) {
+        const int t = target[g];
+        if (t < 0 || t >= M || nctl[g] < 0 || nctl[g] > 2) return -1;
+        for (int k = 0; k < nctl[g]; ++k) {
+            const int c = ctl[2 * g + k], v = lvl[2 * g + k];
+            if (c < 0 || c >= M || c == t || v < 0 || v > 2) return -1;
+            if (k == 1 && c == ctl[2 * g]) return -1;
+        }
+        const double *u = U + 18 * g;
+        cplx m[9];
+        for (int e = 0; e < 9; ++e) m[e] = u[2 * e] + I * u[2 * e + 1];
+        for (uint64_t i = 0; i < pw[M]; ++i) {
+            if ((i / pw[t]) % 3 != 0) continue;
+            int on = 1;
+            for (int k = 0; k < nctl[g]; ++k)
+                if ((int)((i / pw[ctl[2 * g + k]]) % 3) != lvl[2 * g + k]) on = 0;
+            if (!on) continue;
+            const cplx a = psi[i], b = psi[i + pw[t]], c = psi[i + 2 * pw[t]];
+            psi[i] = m[0] * a + m[1] * b + m[2] * c;
+            psi[i + pw[t]] = m[3] * a + m[4] * b + m[5] * c;
+            psi[i + 2 * pw[t]] = m[6] * a + m[7] * b + m[8] * c;
+        }
+    }
+    return 0;
+}

@@ -347,4 +347,71 @@ def pin_decoherence_channel(orc):
     assert np.array_equal(c, orc.run(M, recs, psi0))
 
 
+def dense3(M: int, U: np.ndarray, target: int, controls=(), levels=()) -> np.ndarray:
+    """The 3^M x 3^M matrix of one three-level transformation: I plus
+    (U - I) on the target tensored with the projector on each control's
+    level (digit q of the index = particle q, digit 0 least significant)."""
+    factors = []
+    for q in range(M - 1, -1, -1):
+        if q == target:
+            factors.append(np.asarray(U, dtype=np.complex128) - np.eye(3))
+        elif q in controls:
+            P = np.zeros((3, 3))
+            v = levels[list(controls).index(q)]
+            P[v, v] = 1.0
+            factors.append(P)
+        else:
+            factors.append(np.eye(3))
+    return np.eye(3 ** M, dtype=np.complex128) + reduce(np.kron, factors)
+
+
+def pin_qutrit_brute_force(orc):
+    """Three-state model: random pulses (controlled ones too) against dense
+    3^M x 3^M products, M = 1, 2, 3."""
+    for M in (1, 2, 3):
+        c = W.circuit_qutrit(M, 25, seed_circuit=M)
+        x = W.random_state3(M, seed=M, dtype=np.complex128)
+        ref = x.copy()
+        for rec in c["noisy"]:
+            ctl = tuple(int(v) for v in rec["controls"][: int(rec["ncontrols"])])
+            lev = tuple(int(v) for v in rec["levels"][: int(rec["ncontrols"])])
+            ref = dense3(M, W.record3_matrix(rec), int(rec["target"]), ctl, lev) @ ref
+        got = orc.qutrit_apply(x.copy(), c["noisy"])
+        assert np.allclose(got, ref, atol=1e-13, rtol=0)
+        assert abs(np.vdot(got, got).real - 1.0) < 1e-13
+
+
+def pin_qutrit_special_cases(orc):
+    """The discrete Fourier transform on every particle from |0...0> gives
+    3^{-M/2} everywhere; the cyclic level shift applied three times returns
+    the input bit for bit; pulses between levels 0 and 1 on a state without
+    level 2 are the two-state simulation of the same pulses."""
+    M = 4
+    psi = np.zeros(3 ** M, dtype=np.complex128)
+    psi[0] = 1.0
+    orc.qutrit_apply(psi, W.pack3([W.gate3_record(W.mat_dft3(), q) for q in range(M)]))
+    assert np.allclose(psi, 3.0 ** (-M / 2), atol=1e-15)
+    shift = np.roll(np.eye(3), 1, axis=0)
+    x = W.random_state3(M, seed=9, dtype=np.complex128)
+    y = orc.qutrit_apply(x.copy(), W.pack3([W.gate3_record(shift, 2, (0,), (1,))] * 3))
+    assert np.array_equal(x, y)
+    rng = np.random.default_rng(4)
+    recs3, recs2 = [], []
+    for _ in range(12):
+        t = int(rng.integers(M))
+        th, ph = float(rng.uniform(0, 6.3)), float(rng.uniform(0, 6.3))
+        U3 = W.mat_pulse3(0, 1, th, ph)
+        ctl = (int(rng.choice([q for q in range(M) if q != t])),) if rng.random() < 0.5 else ()
+        recs3.append(W.gate3_record(U3, t, ctl, (1,) * len(ctl)))
+        recs2.append(W.gate_record(U3[:2, :2], t, ctl))
+    x2 = _rand_state(rng, M)
+    x3 = np.zeros(3 ** M, dtype=np.complex128)
+    for i in range(1 << M):
+        x3[sum(((i >> q) & 1) * 3 ** q for q in range(M))] = x2[i]
+    orc.qutrit_apply(x3, W.pack3(recs3))
+    y2 = orc.run(M, W._pack(recs2), x2)
+    for i in range(1 << M):
+        assert abs(x3[sum(((i >> q) & 1) * 3 ** q for q in range(M))] - y2[i]) < 1e-14
+
+
 PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

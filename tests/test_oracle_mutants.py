@@ -42,6 +42,20 @@ MUTANTS = {
     "decoherence_no_renormalisation": [("const double s = sqrt(N / (N - gamma * P1));", "const double s = 1.0;")],
     "decoherence_dephasing_sign": [("const double Rz[8] = {cos(h), -sin(h), 0, 0, 0, 0, cos(h), sin(h)};",
                                     "const double Rz[8] = {cos(h), sin(h), 0, 0, 0, 0, cos(h), -sin(h)};")],
+    "qutrit_binary_stride": [("const cplx a = psi[i], b = psi[i + pw[t]], c = psi[i + 2 * pw[t]];",
+                              "const uint64_t s2 = (uint64_t)1 << t; "
+                              "const cplx a = psi[i], b = psi[i + s2], c = psi[i + 2 * s2];"),
+                             ("psi[i + pw[t]] = m[3] * a + m[4] * b + m[5] * c;",
+                              "psi[i + s2] = m[3] * a + m[4] * b + m[5] * c;"),
+                             ("psi[i + 2 * pw[t]] = m[6] * a + m[7] * b + m[8] * c;",
+                              "psi[i + 2 * s2] = m[6] * a + m[7] * b + m[8] * c;")],
+    "qutrit_transposed": [("psi[i] = m[0] * a + m[1] * b + m[2] * c;", "psi[i] = m[0] * a + m[3] * b + m[6] * c;"),
+                          ("psi[i + pw[t]] = m[3] * a + m[4] * b + m[5] * c;",
+                           "psi[i + pw[t]] = m[1] * a + m[4] * b + m[7] * c;"),
+                          ("psi[i + 2 * pw[t]] = m[6] * a + m[7] * b + m[8] * c;",
+                           "psi[i + 2 * pw[t]] = m[2] * a + m[5] * b + m[8] * c;")],
+    "qutrit_control_level_ignored": [("if ((int)((i / pw[ctl[2 * g + k]]) % 3) != lvl[2 * g + k]) on = 0;",
+                                      "if ((int)((i / pw[ctl[2 * g + k]]) % 3) == 0) on = 0;")],
     "decoherence_jump_on_zero": [("K[2] = sqrt(gamma) * sqrt(N / (gamma * P1));",
                                   "K[4] = sqrt(gamma) * sqrt(N / (gamma * P1));")],
 }

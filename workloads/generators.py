@@ -384,3 +384,97 @@ def circuit_gradual(M: int, start: int = 4, per_qubit: int = 16, sigma: float = 
     ax = np.array(axes, dtype=np.float64)
     eps = np.random.default_rng(seed_err).normal(0.0, sigma, size=len(recs))
     return {"M": M, "ideal": ideal, "axes": ax, "eps": eps, "noisy": with_errors(ideal, ax, eps)}
+
+
+# ------------------------------------------------------------------ qutrits
+# The three-state model (Section 2.0): 3^M amplitudes, digit q of the base-3
+# index = the level of particle q.  One transformation record: a 3x3 matrix on
+# a target particle, applied where each control particle is at its level.
+GATE3_DTYPE = np.dtype(
+    [("U", "<f8", (18,)), ("target", "<i4"), ("ncontrols", "<i4"), ("controls", "<i4", (2,)),
+     ("levels", "<i4", (2,))]
+)
+assert GATE3_DTYPE.itemsize == 168
+
+
+def mat_pulse3(j: int, k: int, theta: float, phi: float = 0.0) -> np.ndarray:
+    """A laser pulse between levels j and k of one particle (a rotation by
+    theta with phase phi in that two-level subspace; the third level
+    untouched)."""
+    U = np.eye(3, dtype=np.complex128)
+    c, s = np.cos(theta / 2), np.sin(theta / 2)
+    U[j, j] = c
+    U[k, k] = c
+    U[j, k] = -1j * np.exp(-1j * phi) * s
+    U[k, j] = -1j * np.exp(1j * phi) * s
+    return U
+
+
+def mat_dft3() -> np.ndarray:
+    w = np.exp(2j * np.pi / 3)
+    return np.array([[1, 1, 1], [1, w, w * w], [1, w * w, w]], dtype=np.complex128) / np.sqrt(3)
+
+
+def gate3_record(U: np.ndarray, target: int, controls=(), levels=()) -> np.ndarray:
+    rec = np.zeros((), dtype=GATE3_DTYPE)
+    U = np.asarray(U, dtype=np.complex128).reshape(9)
+    rec["U"][0::2] = U.real
+    rec["U"][1::2] = U.imag
+    rec["target"] = target
+    rec["ncontrols"] = len(controls)
+    for i, (c, v) in enumerate(zip(controls, levels)):
+        rec["controls"][i] = c
+        rec["levels"][i] = v
+    return rec
+
+
+def pack3(recs) -> np.ndarray:
+    out = np.zeros(len(recs), dtype=GATE3_DTYPE)
+    for i, r in enumerate(recs):
+        out[i] = r
+    return out
+
+
+def record3_matrix(rec) -> np.ndarray:
+    u = rec["U"]
+    return (u[0::2] + 1j * u[1::2]).reshape(3, 3)
+
+
+def records3_to_arrays(recs: np.ndarray):
+    recs = np.ascontiguousarray(recs, dtype=GATE3_DTYPE)
+    return (np.ascontiguousarray(recs["U"]), np.ascontiguousarray(recs["target"]),
+            np.ascontiguousarray(recs["ncontrols"]), np.ascontiguousarray(recs["controls"]),
+            np.ascontiguousarray(recs["levels"]))
+
+
+def circuit_qutrit(M: int, n_gates: int, sigma: float = 1e-3, seed_circuit=0, seed_err=1):
+    """Random laser pulses on M three-level particles (as the detailed model
+    of Section 2.0 runs its gates): each a rotation between two levels of a
+    random particle by theta ~ U[0, 2 pi) with phase phi ~ U[0, 2 pi), a third
+    of them conditioned on another particle being at level 1 or 2.  The noisy
+    copy deviates every angle by a Gaussian eps (sigma)."""
+    rng = np.random.default_rng(seed_circuit)
+    eps = np.random.default_rng(seed_err).normal(0.0, sigma, size=n_gates)
+    ideal, noisy = [], []
+    pairs = [(0, 1), (1, 2), (0, 2)]
+    for g in range(n_gates):
+        t = int(rng.integers(M))
+        j, k = pairs[int(rng.integers(3))]
+        theta = float(rng.uniform(0, 2 * np.pi))
+        phi = float(rng.uniform(0, 2 * np.pi))
+        ctl, lev = (), ()
+        if M > 1 and rng.random() < 1 / 3:
+            ctl = (int(rng.choice([q for q in range(M) if q != t])),)
+            lev = (int(rng.integers(1, 3)),)
+        ideal.append(gate3_record(mat_pulse3(j, k, theta, phi), t, ctl, lev))
+        noisy.append(gate3_record(mat_pulse3(j, k, theta + eps[g], phi), t, ctl, lev))
+    return {"M": M, "ideal": pack3(ideal), "noisy": pack3(noisy), "eps": eps}
+
+
+def random_state3(M: int, seed: int = 2, dtype=np.complex64) -> np.ndarray:
+    """A random normalised complex Gaussian vector of 3^M amplitudes."""
+    rng = np.random.default_rng(seed)
+    n = 3 ** M
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x /= np.linalg.norm(x)
+    return x.astype(dtype)
