@@ -428,6 +428,40 @@ typedef void *(*qsim_device_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx
 typedef void (*qsim_device_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *ctx);
 int qsim_set_allocator(qsim_device_alloc_fn alloc, qsim_device_free_fn free, void *ctx);
 
+/* ------------------------------------------------------------- qutrits */
+
+/* The three-state model (Section 2.0: the detailed model with a third,
+ * temporary level per particle, 3^M states; Sections 3.0-3.1).  The
+ * amplitudes of M three-level particles are 3^M complex numbers, the index
+ * written in base 3 with digit q = the level of particle q (digit 0 least
+ * significant).  A transformation is a 3x3 matrix U (row-major, re/im
+ * interleaved: 18 doubles) on a target particle, applied to every triple of
+ * states differing only in the target's level, (a_i, a_{i+3^t}, a_{i+2 3^t})
+ * for each i with digit t = 0, where each control particle controls[k] is at
+ * level levels[k].  168 bytes, no padding. */
+typedef struct qsim_gate3 {
+    double U[18];
+    int32_t target;
+    int32_t ncontrols;   /* 0, 1 or 2 */
+    int32_t controls[2]; /* distinct particles, != target */
+    int32_t levels[2];   /* 0, 1 or 2 */
+} qsim_gate3;
+
+/* Apply n transformations in order to caller-owned device amplitudes (3^M
+ * interleaved complex numbers, 16-byte aligned), on cuda_stream (NULL =
+ * legacy default), one kernel launch each; returns once queued.  M in
+ * [1, 21].  QSIM_EINVAL for an out-of-range particle or level, a repeated
+ * particle, or a non-finite matrix (nothing is queued then). */
+int qsim_qutrit_apply(void *device_amps, int M, qsim_prec prec, const qsim_gate3 *gates, size_t n,
+                      void *cuda_stream);
+
+/* out[0] = sum |noisy_i|^2, out[1] + i out[2] = sum conj(ideal_i) noisy_i over
+ * the 3^M amplitudes (FP64, fixed order); ideal_amps may be NULL (then out[1]
+ * = out[2] = 0).  F = out[1]^2 + out[2]^2.  Allocates 3^M / 2^16 x 24 bytes of
+ * device scratch for the call; waits for cuda_stream. */
+int qsim_qutrit_overlap(const void *ideal_amps, const void *noisy_amps, int M, qsim_prec prec, void *cuda_stream,
+                        double out[3]);
+
 /* ---------------------------------------------------------- decoherence */
 
 /* A circuit with decoherence after every operation (Section 3.4: two more

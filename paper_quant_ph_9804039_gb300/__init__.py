@@ -134,6 +134,8 @@ SIGNATURES = [
     ("qsim_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
     ("qsim_server_destroy", None, [_vp]),
     ("qsim_set_allocator", ctypes.c_int, [_vp, _vp, _vp]),
+    ("qsim_qutrit_apply", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    ("qsim_qutrit_overlap", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _dp]),
     ("qsim_run_decoherence", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _dp, _dp, ctypes.c_double,
                                             ctypes.POINTER(ctypes.c_int32), _dp]),
     ("qsim_shard_plan_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t,
@@ -502,6 +504,55 @@ def run_trajectories(M: int, gates, err_axis, eps, fuse_k: int = 0, use_graph: b
 
 def version() -> str:
     return load_library().qsim_version().decode()
+
+
+# qsim_gate3 of include/qsim.h: U[18] doubles, int32 target, ncontrols, controls[2], levels[2]
+GATE3_DTYPE = np.dtype(
+    [("U", "<f8", (18,)), ("target", "<i4"), ("ncontrols", "<i4"), ("controls", "<i4", (2,)),
+     ("levels", "<i4", (2,))]
+)
+assert GATE3_DTYPE.itemsize == 168
+
+
+class QutritState:
+    """3^M amplitudes of M three-level particles on the GPU (a torch tensor);
+    qsim_qutrit_apply / qsim_qutrit_overlap work on its device pointer."""
+
+    def __init__(self, M: int, prec="c64", device=None, stream=None):
+        torch = _torch()
+        load_library()
+        self.M = int(M)
+        self.prec = _prec(prec)
+        dtype = torch.complex64 if self.prec == QSIM_C64 else torch.complex128
+        self.tensor = torch.zeros(3 ** self.M, dtype=dtype, device=device if device is not None else "cuda")
+        self.tensor[0] = 1.0
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.tensor.device)
+
+    def set(self, amps):
+        torch = _torch()
+        a = np.ascontiguousarray(amps, dtype=np.complex64 if self.prec == QSIM_C64 else np.complex128)
+        assert a.size == 3 ** self.M
+        self.tensor.copy_(torch.from_numpy(a))
+        return self
+
+    def get(self) -> np.ndarray:
+        with _torch().cuda.stream(self.stream):
+            return self.tensor.cpu().numpy()
+
+    def apply(self, gates3):
+        g = np.ascontiguousarray(gates3, dtype=GATE3_DTYPE)
+        _check(_lib.qsim_qutrit_apply(_vp(self.tensor.data_ptr()), self.M, self.prec, _vp(g.ctypes.data), len(g),
+                                      _vp(self.stream.cuda_stream)))
+        return self
+
+
+def qutrit_overlap(ideal: QutritState | None, noisy: QutritState):
+    """(norm of noisy, Re, Im of <ideal|noisy>) over 3^M amplitudes."""
+    out = np.zeros(3)
+    _check(load_library().qsim_qutrit_overlap(_vp(ideal.tensor.data_ptr()) if ideal is not None else None,
+                                              _vp(noisy.tensor.data_ptr()), noisy.M, noisy.prec,
+                                              _vp(noisy.stream.cuda_stream), out.ctypes.data_as(_dp)))
+    return out
 
 
 def run_decoherence(state: State, gates, delta, r, gamma: float):

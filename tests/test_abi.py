@@ -92,3 +92,23 @@ def test_set_allocator_host_checks():
     assert lib.qsim_set_allocator(ctypes.cast(fa, ctypes.c_void_p), None, None) == qs.QSIM_EINVAL
     assert b"both" in lib.qsim_last_error()
     assert lib.qsim_set_allocator(None, None, None) == qs.QSIM_OK
+
+
+def test_gate3_record_layout_matches_workloads():
+    from workloads.generators import GATE3_DTYPE
+    assert qs.GATE3_DTYPE == GATE3_DTYPE and qs.GATE3_DTYPE.itemsize == 168
+
+
+def test_qutrit_and_decoherence_host_checks():
+    """Argument checks before any CUDA call."""
+    lib = qs.load_library()
+    assert lib.qsim_qutrit_apply(None, 3, 0, None, 0, None) == qs.QSIM_EINVAL
+    assert lib.qsim_qutrit_apply(ctypes.c_void_p(16), 22, 0, None, 0, None) == qs.QSIM_EINVAL
+    assert b"particles" in lib.qsim_last_error()
+    from workloads.generators import gate3_record, pack3
+    import numpy as np
+    g = pack3([gate3_record(np.eye(3), 0, (0,), (1,))])  # control == target
+    assert lib.qsim_qutrit_apply(ctypes.c_void_p(16), 3, 0, ctypes.c_void_p(g.ctypes.data), 1, None) == qs.QSIM_EINVAL
+    g = pack3([gate3_record(np.eye(3), 1, (0,), (3,))])  # level 3
+    assert lib.qsim_qutrit_apply(ctypes.c_void_p(16), 3, 0, ctypes.c_void_p(g.ctypes.data), 1, None) == qs.QSIM_EINVAL
+    assert lib.qsim_run_decoherence(None, None, 0, None, None, 0.1, None, None) == qs.QSIM_EINVAL
