@@ -311,16 +311,16 @@ def oracle_size(M: int) -> int:
     return m
 
 
-def oracle_sample(M, gates, x, budget_s: float, min_gates: int = 3):
-    """Time the CPU oracle (all host threads) on the first gates of the noisy
-    circuit, at the workload's M if the host has the memory (else the largest
-    M that fits), for about budget_s seconds after one untimed gate (which
-    touches every page of the state).  Returns (amp-updates/s, gates applied,
-    seconds, threads, M used)."""
+def oracle_sample(M, gates, x, budget_s: float, min_gates: int = 3, nthreads=None, max_M=None):
+    """Time the CPU oracle (all host threads, or nthreads) on the first gates
+    of the noisy circuit, at the workload's M if the host has the memory
+    (else the largest M that fits, or max_M), for about budget_s seconds after
+    one untimed gate (which touches every page of the state).  Returns
+    (amp-updates/s, gates applied, seconds, threads, M used)."""
     import oracle
     orc = oracle.Oracle()
-    nt = oracle.default_threads()
-    Ms = oracle_size(M)
+    nt = nthreads or oracle.default_threads()
+    Ms = oracle_size(M) if max_M is None else min(oracle_size(M), max_M)
     if x is not None and Ms == M:
         psi = x.astype(np.complex128)
     else:
@@ -499,6 +499,11 @@ def run_brickwork(args, rank, world, local):
     for m, d in modes.items():
         d["speedup_of_unfused"] = (modes["unfused"]["ms_per_step"] / d["ms_per_step"]) if "unfused" in modes else None
     result["modes"] = modes
+    if args.mode == "auto":
+        try:
+            result["auto_rates"] = qs.tune_rates("c64", specialize=spec)
+        except qs.QsimError as e:
+            result["auto_rates"] = {"error": str(e)}
     del ideal, noisy
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
@@ -636,13 +641,19 @@ def run_ours(args, rank, world, local):
         result["single_gate"] = bench_single_gate(stream)
         result["batched"] = bench_trajectories(world, result["clocks"].get("sm_mhz"))
         result["subspace"] = bench_subspace(world, stream)
+        result["decoherence"] = bench_decoherence(world, stream)
+        result["qutrit"] = bench_qutrit(world, stream)
         result["serving"] = bench_serving(args.serve_requests, world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, ng, dt, nt, Ms = oracle_sample(wl["M"], c["noisy"], x, budget_s=15.0)
+        v1, ng1, dt1, _, Ms1 = oracle_sample(wl["M"], c["noisy"], None, budget_s=5.0, nthreads=1, max_M=26)
         result["cpu_baseline"] = {"value": v, "unit": "amp-updates/s", "cores": nt, "kind": "oracle",
                                   "sample": f"first {ng} gates of the noisy circuit at M={Ms} "
-                                            f"(complex128), {dt:.1f} s"}
+                                            f"(complex128), {dt:.1f} s",
+                                  "one_core": {"value": v1, "unit": "amp-updates/s", "cores": 1,
+                                               "sample": f"first {ng1} gates of the noisy circuit at M={Ms1} "
+                                                         f"(complex128), {dt1:.1f} s"}}
     if rank == 0:
         print(json.dumps(result), flush=True)
 
@@ -785,6 +796,64 @@ def bench_subspace(world, stream):
     out["speedup"] = out["flat"]["ms_per_step"] / out["subspace"]["ms_per_step"]
     out["F_difference"] = abs(out["flat"]["F"] - out["subspace"]["F"])
     del a, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_decoherence(world, stream):
+    """Decoherence after every operation (Section 3.4 reading): M=28,
+    complex64, 100 random gates with dephasing kicks (sigma 1e-3) and
+    amplitude damping gamma = 1e-3; one pass over the vector per operation
+    (16 bytes per amplitude), timed with CUDA events."""
+    import torch
+    import paper_quant_ph_9804039_gb300 as qs
+    from workloads import generators as W
+    M, n = 28, 100
+    c = W.circuit_c1_random(M, n, 1e-3, seed_circuit=5, seed_err=6)
+    rng = np.random.default_rng(7)
+    delta = rng.normal(0.0, 1e-3, n)
+    r = rng.random(n)
+    st = qs.State(M, stream=stream).set(W.random_state(M, seed=2))
+    qs.run_decoherence(st, c["noisy"][:4], delta[:4], r[:4], 1e-3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    jumps, p = qs.run_decoherence(st, c["noisy"], delta, r, 1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    peak, _ = measured_peaks()
+    gbs = (n + 1) * 16.0 * float(1 << M) / (ms / 1e3) / 1e9
+    out = {"workload": "decoherence-m28-c64", "M": M, "operations": n, "gamma": 1e-3, "ms": ms,
+           "ms_per_operation": ms / n, "launches": n + 1, "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+           "jumps": int(jumps.sum()), "amp_updates_per_s": world * n * float(1 << M) / (ms / 1e3),
+           "passes_per_operation": 1.0, "paper_transformations_per_operation": 3}
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_qutrit(world, stream):
+    """The three-state model: M=18 particles (3^18 complex64 amplitudes,
+    3.1 GB), 40 laser pulses (a third controlled), one launch per pulse;
+    algorithmic bytes 16 per amplitude per uncontrolled pulse (a controlled
+    pulse reads and writes the third of the triples its control selects)."""
+    import torch
+    import paper_quant_ph_9804039_gb300 as qs
+    from workloads import generators as W
+    M = 18
+    c = W.circuit_qutrit(M, 40, seed_circuit=18)
+    st = qs.QutritState(M, stream=stream)
+    st.apply(c["noisy"][:2])
+    ms = _events_ms(lambda: st.apply(c["noisy"]), 3, stream)
+    nct = int(np.sum(c["noisy"]["ncontrols"] > 0))
+    byts = 16.0 * 3 ** M * ((len(c["noisy"]) - nct) + nct / 3.0)
+    peak, _ = measured_peaks()
+    gbs = byts / (ms / 1e3) / 1e9
+    out = {"workload": "qutrit-m18-c64", "M": M, "pulses": len(c["noisy"]), "controlled": nct, "ms": ms,
+           "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+           "amp_updates_per_s": world * len(c["noisy"]) * float(3 ** M) / (ms / 1e3)}
+    del st
     torch.cuda.empty_cache()
     return out
 

@@ -194,9 +194,9 @@ def tune_rates(prec="c64", specialize=True) -> dict:
     import json
     lib = load_library()
     n = ctypes.c_int64(0)
-    _check(lib.qsim_tune_rates(_prec(prec), int(bool(specialize)), None, 0, ctypes.byref(n)))
-    buf = ctypes.create_string_buffer(int(n.value))
-    _check(lib.qsim_tune_rates(_prec(prec), int(bool(specialize)), buf, n.value, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(4096)  # one call: a second one could read the cache and differ
+    _check(lib.qsim_tune_rates(_prec(prec), int(bool(specialize)), buf, len(buf), ctypes.byref(n)))
+    assert n.value <= len(buf)
     return json.loads(buf.value.decode())
 
 

@@ -21,6 +21,7 @@ void set_error(const char *fmt, ...) {
 
 int cuda_fail(cudaError_t e, const char *what) {
     set_error("CUDA error %d (%s) in %s", int(e), cudaGetErrorString(e), what);
+    cudaGetLastError();  // a non-sticky error is reported once, not again by the next launch check
     return e == cudaErrorMemoryAllocation ? QSIM_ENOMEM : QSIM_ECUDA;
 }
 

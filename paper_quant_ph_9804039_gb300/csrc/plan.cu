@@ -2119,6 +2119,14 @@ void qsim_plan_destroy(qsim_plan *p) {
 
 int qsim_plan_status(const qsim_plan *p) {
     if (!p) { set_error("plan is NULL"); return QSIM_EINVAL; }
+    if (p->subspace) {  // the segments' plans (every record is read and cleared)
+        int first = QSIM_OK;
+        for (const qsim_plan *c : p->seg_plans)
+            if (int rc = qsim_plan_status(c)) first = first ? first : rc;
+        if (p->relabel)
+            if (int rc = qsim_plan_status(p->relabel)) first = first ? first : rc;
+        return first;
+    }
     int v = 0;
     QS_CUDA(cudaDeviceSynchronize());
     QS_CUDA(cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
