@@ -1202,23 +1202,33 @@ FusedDesc fused_desc(int M, int k, const int *bq) {
     return d;
 }
 
-// Greedy grouping into blocks of at most k qubits (every qubit of a gate,
-// controls included, joins the block), padded to exactly k qubits with the
-// lowest free ones.
-void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
-    const int M = p->M;
-    std::vector<int> rem(p->gates.size());
+// Grouping into blocks of k qubits (every qubit of a gate, controls
+// included, belongs to the block).  A gate may join a block ahead of earlier
+// gates left for later blocks only if it commutes with each of them: neither
+// gate's non-diagonal target is a qubit of the other.  For each block the
+// candidates are the greedy set (gates taken in order while their qubits fit,
+// padded to k with the lowest free qubits) and every window of k consecutive
+// qubits; the candidate that takes the most remaining gates wins (on the
+// 33-qubit brickwork: 75 blocks per circuit instead of the greedy 108).
+struct FusedGroup {
+    uint64_t Q;
+    std::vector<int> take;
+};
+std::vector<FusedGroup> fused_groups(const std::vector<Gate> &gates, int k, int M) {
+    std::vector<int> rem(gates.size());
     for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
-    const size_t per = fused_rimg_halves(k);
+    std::vector<FusedGroup> out;
+    std::vector<int> take, keep, best_take, best_keep;
     while (!rem.empty()) {
+        // the greedy candidate
         uint64_t defN = 0, defA = 0, Q = 0;
-        std::vector<int> take, keep;
+        take.clear();
+        keep.clear();
         for (int gi : rem) {
-            const Gate &g = p->gates[gi];
+            const Gate &g = gates[size_t(gi)];
             const uint64_t N = g.nondiag() ? bit(g.t) : 0;
             const uint64_t A = bit(g.t) | g.cmask;
-            const bool blocked = (N & defA) || (A & defN);
-            if (!blocked && __builtin_popcountll(Q | A) <= k) {
+            if (!((N & defA) || (A & defN)) && __builtin_popcountll(Q | A) <= k) {
                 take.push_back(gi);
                 Q |= A;
             } else {
@@ -1228,6 +1238,45 @@ void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
             }
         }
         for (int q = 0; q < M && __builtin_popcountll(Q) < k; ++q) Q |= bit(q);
+        uint64_t bestQ = Q;
+        best_take.swap(take);
+        best_keep.swap(keep);
+        // the windows of k consecutive qubits
+        for (int s = 0; s + k <= M; ++s) {
+            const uint64_t W = ((uint64_t(1) << k) - 1) << s;
+            defN = defA = 0;
+            take.clear();
+            keep.clear();
+            for (int gi : rem) {
+                const Gate &g = gates[size_t(gi)];
+                const uint64_t N = g.nondiag() ? bit(g.t) : 0;
+                const uint64_t A = bit(g.t) | g.cmask;
+                if (!((N & defA) || (A & defN)) && !(A & ~W)) {
+                    take.push_back(gi);
+                } else {
+                    keep.push_back(gi);
+                    defN |= N;
+                    defA |= A;
+                }
+            }
+            if (take.size() > best_take.size()) {
+                bestQ = W;
+                best_take.swap(take);
+                best_keep.swap(keep);
+            }
+        }
+        out.push_back({bestQ, best_take});
+        rem.swap(best_keep);
+    }
+    return out;
+}
+
+void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
+    const int M = p->M;
+    const size_t per = fused_rimg_halves(k);
+    for (const FusedGroup &grp : fused_groups(p->gates, k, M)) {
+        const uint64_t Q = grp.Q;
+        const std::vector<int> &take = grp.take;
         int bq[8], nb = 0;
         for (int q = 0; q < M; ++q)
             if (Q & bit(q)) bq[nb++] = q;
@@ -1241,7 +1290,6 @@ void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
         block_rimg(U, k, rimg.data() + st.rimg);
         st.bytes = 2.0 * std::ldexp(1.0, M) * 8.0;
         p->steps.push_back(st);
-        rem.swap(keep);
     }
 }
 
@@ -1256,32 +1304,11 @@ void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
 // Seconds of the fused blocks of width k for these gates (the grouping of
 // plan_fused, without building the matrices).
 double model_fused(const std::vector<Gate> &gates, int k, int M, const ModelRates &r, int *nblocks) {
-    std::vector<int> rem(gates.size());
-    for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
     const double bytes = 16.0 * std::ldexp(1.0, M);
     double t = 0;
-    int blocks = 0;
-    while (!rem.empty()) {
-        uint64_t defN = 0, defA = 0, Q = 0;
-        std::vector<int> keep;
-        for (int gi : rem) {
-            const Gate &g = gates[size_t(gi)];
-            const uint64_t N = g.nondiag() ? bit(g.t) : 0;
-            const uint64_t A = bit(g.t) | g.cmask;
-            if (!((N & defA) || (A & defN)) && __builtin_popcountll(Q | A) <= k) {
-                Q |= A;
-            } else {
-                keep.push_back(gi);
-                defN |= N;
-                defA |= A;
-            }
-        }
-        for (int q = 0; q < M && __builtin_popcountll(Q) < k; ++q) Q |= bit(q);
-        t += bytes / ((Q & 31u) ? r.fused_staged[k] : r.fused_direct[k]);
-        ++blocks;
-        rem.swap(keep);
-    }
-    if (nblocks) *nblocks = blocks;
+    const std::vector<FusedGroup> groups = fused_groups(gates, k, M);
+    for (const FusedGroup &grp : groups) t += bytes / ((grp.Q & 31u) ? r.fused_staged[k] : r.fused_direct[k]);
+    if (nblocks) *nblocks = int(groups.size());
     return t;
 }
 

@@ -20,9 +20,19 @@ NT = max(1, os.cpu_count() or 1)
 
 
 def _case(M, n, gamma, seed, x=None):
+    """n random gates (Haar SU(2) times a phase, Rz, X; 0..2 controls when M
+    allows), dephasing angles and jump draws."""
     rng = np.random.default_rng(seed)
-    c = W.circuit_c1_random(M, n, 1e-3, seed_circuit=seed, seed_err=seed + 1)
-    recs = c["noisy"]
+    recs = []
+    for _ in range(n):
+        t = int(rng.integers(M))
+        nc = int(rng.integers(0, min(2, M - 1) + 1))
+        ctl = [int(v) for v in rng.choice([q for q in range(M) if q != t], size=nc, replace=False)] if nc else []
+        kind = int(rng.integers(3))
+        U = (W.mat_haar_su2(rng) * np.exp(1j * rng.uniform(0, 6.3)) if kind == 0 else
+             W.mat_rz(float(rng.uniform(0, 6.3))) if kind == 1 else W.mat_x())
+        recs.append(W.gate_record(U, t, ctl))
+    recs = W._pack(recs)
     delta = rng.normal(0.0, 0.05, len(recs))
     r = rng.random(len(recs))
     return recs, delta, r
