@@ -69,18 +69,40 @@ __device__ void block_sum2(double &a, double &b, double (*sh)[kThreads / 32]) {
     }
 }
 
-template <typename T2>
-__device__ __forceinline__ void scale2(T2 &v, double s) {
-    using R = decltype(v.x);
-    const R hi = R(s), lo = R(s - double(hi));
+// v * (hi + lo): a real factor carried as two values of the state precision
+template <typename T2, typename R>
+__device__ __forceinline__ void scale2(T2 &v, R hi, R lo) {
     v.x = fma(v.x, hi, v.x * lo);
     v.y = fma(v.y, hi, v.y * lo);
 }
 
+// |v|^2 in the state precision
 template <typename T2>
-__device__ __forceinline__ double weight(const T2 &v) {
-    return double(v.x) * double(v.x) + double(v.y) * double(v.y);
+__device__ __forceinline__ auto weight(const T2 &v) -> decltype(v.x) {
+    return fma(v.x, v.x, v.y * v.y);
 }
+
+// A running sum of weights: complex64 terms are added in float over groups of
+// 8 loop iterations, then in double (FP64 is a slow pipe on this GPU);
+// complex128 terms in double.
+template <typename R>
+struct WSum {
+    double d = 0.0;
+    R f = R(0);
+    int n = 0;
+    __device__ __forceinline__ void add(R v) { f += v; }
+    __device__ __forceinline__ void next() {
+        if (sizeof(R) == 8) {
+            d += double(f);
+            f = R(0);
+        } else if (++n == 8) {
+            d += double(f);
+            f = R(0);
+            n = 0;
+        }
+    }
+    __device__ __forceinline__ double total() const { return d + double(f); }
+};
 
 template <typename T2>
 __global__ void __launch_bounds__(kThreads) k_decoh(T2 *__restrict__ a, int M, DecohOp op,
@@ -120,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_decoh(T2 *__restrict__ a, int M, D
     const bool has_k = op.tp >= 0, has_u = op.t >= 0;
     const bool kjump = has_k && kmat[2] != 0.0;
     const double k0 = has_k ? kmat[0] : 1.0, k1 = has_k ? kmat[1] : 1.0;
+    const R k0h = R(k0), k0l = R(k0 - double(k0h)), k1h = R(k1), k1l = R(k1 - double(k1h));
     T2 uh[4], ul[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -154,11 +177,11 @@ __global__ void __launch_bounds__(kThreads) k_decoh(T2 *__restrict__ a, int M, D
     auto damp = [&](T2 &lo, T2 &hi) {
         if (kjump) {
             lo = hi;
-            scale2(lo, k1);
+            scale2(lo, k1h, k1l);
             hi = mk(R(0), R(0));
         } else {
-            scale2(lo, k0);
-            scale2(hi, k1);
+            scale2(lo, k0h, k0l);
+            scale2(hi, k1h, k1l);
         }
     };
     // the gate and its dephasing on one pair (lo: bit t = 0); where a control
@@ -173,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_decoh(T2 *__restrict__ a, int M, D
         lo = cmad2x(uh[0], ul[0], x, uh[1], ul[1], y);
         hi = cmad2x(uh[2], ul[2], x, uh[3], ul[3], y);
     };
-    double sP1 = 0.0, sN = 0.0;
+    WSum<R> wP1, wN;
     const uint64_t stride = uint64_t(gridDim.x) * kThreads;
     if (has_k && has_u && op.tp != op.t) {
         const int lo_b = min(op.tp, op.t), hi_b = max(op.tp, op.t);
@@ -190,8 +213,11 @@ __global__ void __launch_bounds__(kThreads) k_decoh(T2 *__restrict__ a, int M, D
             a[i | bt] = v01;
             a[i | bp] = v10;
             a[i | bp | bt] = v11;
-            sP1 += weight(v01) + weight(v11);
-            sN += weight(v00) + weight(v01) + weight(v10) + weight(v11);
+            const R w01 = weight(v01), w11 = weight(v11);
+            wP1.add(w01 + w11);
+            wN.add((weight(v00) + weight(v10)) + (w01 + w11));
+            wP1.next();
+            wN.next();
         }
     } else if (has_k || has_u) {
         const int b = has_u ? op.t : op.tp;
@@ -204,10 +230,14 @@ __global__ void __launch_bounds__(kThreads) k_decoh(T2 *__restrict__ a, int M, D
             if (has_u) gate(i, v0, v1);
             a[i] = v0;
             a[i | bb] = v1;
-            sP1 += weight(v1);
-            sN += weight(v0) + weight(v1);
+            const R w1 = weight(v1);
+            wP1.add(w1);
+            wN.add(weight(v0) + w1);
+            wP1.next();
+            wN.next();
         }
     }
+    double sP1 = wP1.total(), sN = wN.total();
     block_sum2(sP1, sN, sh);
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = sP1;

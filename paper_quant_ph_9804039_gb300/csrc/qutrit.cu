@@ -28,19 +28,21 @@ template <typename T2>
 struct Gate3K {
     T2 uh[9], ul[9];
     uint64_t st;            // 3^t
-    double inv_st;          // 1 / 3^t
+    uint64_t mst;           // its division multiplier (div_magic)
     int nc;
     uint64_t cpw[2];        // 3^c of each control
-    double cinv[2];
+    uint64_t cm[2];
     int lvl[2];
 };
 
-// q = x / d for d a power of three, x < 2^53
-__device__ __forceinline__ uint64_t div_pow3(uint64_t x, uint64_t d, double inv) {
-    uint64_t q = uint64_t(double(x) * inv);
-    int64_t r = int64_t(x - q * d);
-    if (r < 0) --q;
-    else if (r >= int64_t(d)) ++q;
+// Division by d > 1 through a 64-bit multiply-high: with m = floor(2^64 / d) + 1
+// (d not a power of two), q = mulhi(x, m) is floor(x / d) or one more, for
+// x < 2^40; one compare corrects it.  Integer pipes only (FP64 is slow here).
+__host__ uint64_t div_magic(uint64_t d) { return d > 1 ? ~uint64_t(0) / d + 1 : 0; }
+__device__ __forceinline__ uint64_t div_pow3(uint64_t x, uint64_t d, uint64_t m) {
+    if (d == 1) return x;
+    uint64_t q = __umul64hi(x, m);
+    if (q * d > x) --q;
     return q;
 }
 
@@ -48,11 +50,11 @@ template <typename T2>
 __global__ void __launch_bounds__(256) k_gate3(T2 *__restrict__ a, uint64_t units, Gate3K<T2> g) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t k = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < units; k += stride) {
-        const uint64_t hi = div_pow3(k, g.st, g.inv_st);
+        const uint64_t hi = div_pow3(k, g.st, g.mst);
         const uint64_t i = hi * 3 * g.st + (k - hi * g.st);
         bool on = true;
         for (int c = 0; c < g.nc; ++c) {
-            const uint64_t q = div_pow3(i, g.cpw[c], g.cinv[c]);
+            const uint64_t q = div_pow3(i, g.cpw[c], g.cm[c]);
             on = on && int(q % 3) == g.lvl[c];
         }
         if (!on) continue;
@@ -170,11 +172,11 @@ int apply(void *amps, int M, const qsim_gate3 *gates, size_t n, cudaStream_t s) 
             }
         }
         g.st = pow3(x.target);
-        g.inv_st = 1.0 / double(g.st);
+        g.mst = div_magic(g.st);
         g.nc = x.ncontrols;
         for (int c = 0; c < x.ncontrols; ++c) {
             g.cpw[c] = pow3(x.controls[c]);
-            g.cinv[c] = 1.0 / double(g.cpw[c]);
+            g.cm[c] = div_magic(g.cpw[c]);
             g.lvl[c] = x.levels[c];
         }
         k_gate3<T2><<<grid, 256, 0, s>>>(static_cast<T2 *>(amps), units, g);
