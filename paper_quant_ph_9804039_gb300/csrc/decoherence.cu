@@ -202,40 +202,22 @@ __global__ void __launch_bounds__(kThreads) k_decoh(T2 *__restrict__ a, int M, D
         const int lo_b = min(op.tp, op.t), hi_b = max(op.tp, op.t);
         const uint64_t bp = uint64_t(1) << op.tp, bt = uint64_t(1) << op.t;
         const uint64_t units = uint64_t(1) << (M - 2);
-        // two quadruples per iteration, all eight loads issued before any use
-        for (uint64_t k = uint64_t(blockIdx.x) * kThreads + threadIdx.x; k < units; k += 2 * stride) {
-            const bool two = k + stride < units;
+        for (uint64_t k = uint64_t(blockIdx.x) * kThreads + threadIdx.x; k < units; k += stride) {
             const uint64_t i = insert0(insert0(k, lo_b), hi_b);
-            const uint64_t j = two ? insert0(insert0(k + stride, lo_b), hi_b) : i;
-            T2 v[2][4];  // v[q][<tp bit><t bit>]
-            v[0][0] = a[i];
-            v[0][1] = a[i | bt];
-            v[0][2] = a[i | bp];
-            v[0][3] = a[i | bp | bt];
-            if (two) {
-                v[1][0] = a[j];
-                v[1][1] = a[j | bt];
-                v[1][2] = a[j | bp];
-                v[1][3] = a[j | bp | bt];
-            }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (q == 1 && !two) break;
-                const uint64_t b0 = q ? j : i;
-                damp(v[q][0], v[q][2]);
-                damp(v[q][1], v[q][3]);
-                gate(b0, v[q][0], v[q][1]);
-                gate(b0 | bp, v[q][2], v[q][3]);
-                a[b0] = v[q][0];
-                a[b0 | bt] = v[q][1];
-                a[b0 | bp] = v[q][2];
-                a[b0 | bp | bt] = v[q][3];
-                const R w01 = weight(v[q][1]), w11 = weight(v[q][3]);
-                wP1.add(w01 + w11);
-                wN.add((weight(v[q][0]) + weight(v[q][2])) + (w01 + w11));
-                wP1.next();
-                wN.next();
-            }
+            T2 v00 = a[i], v01 = a[i | bt], v10 = a[i | bp], v11 = a[i | bp | bt];  // v<tp bit><t bit>
+            damp(v00, v10);
+            damp(v01, v11);
+            gate(i, v00, v01);
+            gate(i | bp, v10, v11);
+            a[i] = v00;
+            a[i | bt] = v01;
+            a[i | bp] = v10;
+            a[i | bp | bt] = v11;
+            const R w01 = weight(v01), w11 = weight(v11);
+            wP1.add(w01 + w11);
+            wN.add((weight(v00) + weight(v10)) + (w01 + w11));
+            wP1.next();
+            wN.next();
         }
     } else if (has_k || has_u) {
         const int b = has_u ? op.t : op.tp;
