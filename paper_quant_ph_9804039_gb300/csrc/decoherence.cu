@@ -105,7 +105,7 @@ struct WSum {
 };
 
 template <typename T2>
-__global__ void __launch_bounds__(kThreads, 4) k_decoh(T2 *__restrict__ a, int M, DecohOp op,
+__global__ void __launch_bounds__(kThreads) k_decoh(T2 *__restrict__ a, int M, DecohOp op,
                                                     const double *__restrict__ prev, double *__restrict__ part,
                                                     int *__restrict__ jumps, double *__restrict__ p_out) {
     using R = decltype(a[0].x);
@@ -198,41 +198,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_decoh(T2 *__restrict__ a, int M
     };
     WSum<R> wP1, wN;
     const uint64_t stride = uint64_t(gridDim.x) * kThreads;
-    // the quadruple update of base index i (bit tp and bit t of i are 0)
-    auto quad = [&](uint64_t i, T2 &v00, T2 &v01, T2 &v10, T2 &v11, uint64_t bp) {
-        damp(v00, v10);
-        damp(v01, v11);
-        gate(i, v00, v01);
-        gate(i | bp, v10, v11);
-        const R w01 = weight(v01), w11 = weight(v11);
-        wP1.add(w01 + w11);
-        wN.add((weight(v00) + weight(v10)) + (w01 + w11));
-        wP1.next();
-        wN.next();
-    };
-    if (has_k && has_u && op.tp != op.t && sizeof(R) == 4 && min(op.tp, op.t) >= 1) {
-        // complex64, neither target on qubit 0: quadruples i and i + 1 side by
-        // side, each slot read and written as one 16-byte access
-        const int lo_b = min(op.tp, op.t), hi_b = max(op.tp, op.t);
-        const uint64_t bp = uint64_t(1) << op.tp, bt = uint64_t(1) << op.t;
-        const uint64_t units = uint64_t(1) << (M - 3);
-        float4 *a4 = reinterpret_cast<float4 *>(a);
-        for (uint64_t k = uint64_t(blockIdx.x) * kThreads + threadIdx.x; k < units; k += stride) {
-            const uint64_t i = insert0(insert0(2 * k, lo_b), hi_b);
-            const float4 p00 = a4[i >> 1], p01 = a4[(i | bt) >> 1], p10 = a4[(i | bp) >> 1],
-                         p11 = a4[(i | bp | bt) >> 1];
-            T2 x00 = mk(R(p00.x), R(p00.y)), x01 = mk(R(p01.x), R(p01.y)), x10 = mk(R(p10.x), R(p10.y)),
-               x11 = mk(R(p11.x), R(p11.y));
-            T2 y00 = mk(R(p00.z), R(p00.w)), y01 = mk(R(p01.z), R(p01.w)), y10 = mk(R(p10.z), R(p10.w)),
-               y11 = mk(R(p11.z), R(p11.w));
-            quad(i, x00, x01, x10, x11, bp);
-            quad(i + 1, y00, y01, y10, y11, bp);
-            a4[i >> 1] = make_float4(float(x00.x), float(x00.y), float(y00.x), float(y00.y));
-            a4[(i | bt) >> 1] = make_float4(float(x01.x), float(x01.y), float(y01.x), float(y01.y));
-            a4[(i | bp) >> 1] = make_float4(float(x10.x), float(x10.y), float(y10.x), float(y10.y));
-            a4[(i | bp | bt) >> 1] = make_float4(float(x11.x), float(x11.y), float(y11.x), float(y11.y));
-        }
-    } else if (has_k && has_u && op.tp != op.t) {
+    if (has_k && has_u && op.tp != op.t) {
         const int lo_b = min(op.tp, op.t), hi_b = max(op.tp, op.t);
         const uint64_t bp = uint64_t(1) << op.tp, bt = uint64_t(1) << op.t;
         const uint64_t units = uint64_t(1) << (M - 2);
