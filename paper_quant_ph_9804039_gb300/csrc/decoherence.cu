@@ -82,26 +82,26 @@ __device__ __forceinline__ auto weight(const T2 &v) -> decltype(v.x) {
     return fma(v.x, v.x, v.y * v.y);
 }
 
-// A running sum of weights: complex64 terms are added in float over groups of
-// 8 loop iterations, then in double (FP64 is a slow pipe on this GPU);
-// complex128 terms in double.
+// A running sum of weights.  complex64: a compensated (Kahan) float sum, so
+// the loop issues no FP64 instruction at all (FP64 is a narrow pipe on this
+// GPU: an earlier form that added a float group into a double every 8
+// iterations kept the FP64 pipe 58 % busy and bounded the pass); the
+// per-thread totals are then added in double.  complex128: double.
 template <typename R>
 struct WSum {
-    double d = 0.0;
-    R f = R(0);
-    int n = 0;
-    __device__ __forceinline__ void add(R v) { f += v; }
-    __device__ __forceinline__ void next() {
+    R s = R(0), c = R(0);
+    __device__ __forceinline__ void add(R v) {
         if (sizeof(R) == 8) {
-            d += double(f);
-            f = R(0);
-        } else if (++n == 8) {
-            d += double(f);
-            f = R(0);
-            n = 0;
+            s += v;
+        } else {
+            const R y = v - c;
+            const R t = s + y;
+            c = (t - s) - y;
+            s = t;
         }
     }
-    __device__ __forceinline__ double total() const { return d + double(f); }
+    __device__ __forceinline__ void next() {}
+    __device__ __forceinline__ double total() const { return double(s) - double(c); }
 };
 
 template <typename T2>
