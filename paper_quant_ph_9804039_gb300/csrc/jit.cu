@@ -513,7 +513,8 @@ std::string emit_pass(int idx, const TilePassDesc &d, const std::vector<RegOp> &
 // the error-free state.  Op j of a pass is regops[pass op_begin + j]; its
 // gate is the trajectory op src[j] (index into the plan's op table).
 std::string emit_traj(int M, const std::vector<TilePassDesc> &passes, const std::vector<RegOp> &regops,
-                      const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks) {
+                      const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks,
+                      int lanes) {
     Src out;
     int maxops = 1, maxb = 1;
     bool smem_tile = false;
@@ -528,16 +529,30 @@ std::string emit_traj(int M, const std::vector<TilePassDesc> &passes, const std:
         for (size_t j = 0; j < src[p].size(); ++j) out("%d%s", src[p][j], j + 1 < src[p].size() ? ", " : "");
         out("};\n");
     }
-    out("extern \"C\" __global__ void __launch_bounds__(256, %d)\n", min_blocks);
+    // `lanes` trajectories per CTA (256 threads each) run the same code in
+    // lockstep: the CTA's barriers keep them at the same place in the kernel,
+    // so the instruction cache serves both (with two CTAs per SM at different
+    // places in this long, fully unrolled kernel, warps stalled most on
+    // instruction fetch).  Each lane has its own workspace, tile buffer,
+    // matrices and sums; a lane past the last trajectory repeats its CTA's
+    // first one and writes nothing.
+    out("extern \"C\" __global__ void __launch_bounds__(%d, %d)\n", 256 * lanes, min_blocks);
     out("qs_traj(const QsTrajOp *__restrict__ ops, const double *__restrict__ eps, int n, int T,\n"
         "        const float2 *__restrict__ ideal, float2 *work, double *__restrict__ F_out, unsigned *counter) {\n");
-    if (smem_tile) out("  __shared__ float2 s[%d];\n", 1 << maxb);
-    out("  __shared__ float2 mu[%d][4], ml[%d][4];\n  __shared__ double red[2][8];\n  __shared__ int s_t;\n", maxops,
-        maxops);
-    out("  float2 *ws = work + ((qs_u64)blockIdx.x << %d);\n", M);
-    out("  const qs_u32 tid = threadIdx.x;\n  float2 v[16];\n");
-    out("  for (;;) {\n   if (tid == 0) s_t = int(atomicAdd(counter, 1u));\n   __syncthreads();\n");
-    out("   const int t = s_t;\n   if (t >= T) break;\n   double ore = 0.0, oim = 0.0;\n");
+    out("  const qs_u32 lane = threadIdx.x >> 8;\n");
+    if (smem_tile && lanes > 1)  // dynamic: two tiles of 2^12 pass the 48 KB static limit
+        out("  extern __shared__ float2 s_dyn[];\n  float2 *s = s_dyn + lane * %du;\n", 1u << maxb);
+    else if (smem_tile)
+        out("  __shared__ float2 s[%d];\n", 1 << maxb);
+    out("  __shared__ float2 mu_all[%d][%d][4], ml_all[%d][%d][4];\n", lanes, maxops, lanes, maxops);
+    out("  float2 (*mu)[4] = mu_all[lane];\n  float2 (*ml)[4] = ml_all[lane];\n");
+    out("  __shared__ double red_all[%d][2][8];\n  double (*red)[8] = red_all[lane];\n  __shared__ int s_t;\n", lanes);
+    out("  float2 *ws = work + ((qs_u64)(blockIdx.x * %d + lane) << %d);\n", lanes, M);
+    out("  const qs_u32 tid = threadIdx.x & 255u;\n  float2 v[16];\n");
+    out("  for (;;) {\n   if (threadIdx.x == 0) s_t = int(atomicAdd(counter, %du));\n   __syncthreads();\n", lanes);
+    out("   const int t0 = s_t;\n   if (t0 >= T) break;\n");
+    out("   const bool live = t0 + int(lane) < T;\n   const int t = live ? t0 + int(lane) : t0;\n");
+    out("   double ore = 0.0, oim = 0.0;\n");
     for (size_t p = 0; p < passes.size(); ++p) {
         const TilePassDesc &d = passes[p];
         const int RB = d.b - kRegThreadBits, S = 1 << RB;
@@ -609,7 +624,7 @@ std::string emit_traj(int M, const std::vector<TilePassDesc> &passes, const std:
     out("   for (int o = 16; o > 0; o >>= 1) { ore += __shfl_xor_sync(0xffffffffu, ore, o); "
         "oim += __shfl_xor_sync(0xffffffffu, oim, o); }\n");
     out("   if ((tid & 31) == 0) { red[0][tid >> 5] = ore; red[1][tid >> 5] = oim; }\n   __syncthreads();\n");
-    out("   if (tid == 0) { double a = 0, b = 0; for (int w = 0; w < 8; ++w) { a += red[0][w]; b += red[1][w]; } "
+    out("   if (tid == 0 && live) { double a = 0, b = 0; for (int w = 0; w < 8; ++w) { a += red[0][w]; b += red[1][w]; } "
         "F_out[t] = a * a + b * b; }\n");
     out("   __syncthreads();\n  }\n}\n");
     return out.s;
@@ -695,12 +710,12 @@ int jit_build(const std::vector<const TilePassDesc *> &passes, const std::vector
 
 int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::vector<RegOp> &regops,
                    const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks,
-                   cudaLibrary_t *lib, cudaKernel_t *kernel, std::string *log) {
+                   int lanes, cudaLibrary_t *lib, cudaKernel_t *kernel, std::string *log) {
     if (!nvrtc().ok) {
         if (log) *log = "NVRTC not found";
         return QSIM_EUNSUPPORTED;
     }
-    const std::string text = std::string(kJitHeader) + emit_traj(M, passes, regops, rounds, src, min_blocks);
+    const std::string text = std::string(kJitHeader) + emit_traj(M, passes, regops, rounds, src, min_blocks, lanes);
     std::vector<char> cubin;
     std::string l;
     if (!compile_cubin(text, "qsim_traj.cu", &cubin, &l)) {
@@ -710,6 +725,11 @@ int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::ve
     cudaError_t e = cudaLibraryLoadData(lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e != cudaSuccess) return cuda_fail(e, "loading the trajectory kernel");
     e = cudaLibraryGetKernel(kernel, *lib, "qs_traj");
+    int dev = 0;
+    if (e == cudaSuccess && lanes > 1) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && lanes > 1)
+        e = cudaKernelSetAttributeForDevice(*kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            int(jit_traj_smem_bytes(passes, lanes)), dev);
     if (e != cudaSuccess) {
         cudaLibraryUnload(*lib);
         *lib = nullptr;
@@ -719,6 +739,13 @@ int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::ve
 }
 
 size_t jit_pass_smem_bytes(const TilePassDesc &d) { return size_t(2) * sizeof(float2) << d.b; }
+
+size_t jit_traj_smem_bytes(const std::vector<TilePassDesc> &passes, int lanes) {
+    if (lanes < 2) return 0;
+    int maxb = 1;
+    for (const TilePassDesc &d : passes) maxb = std::max(maxb, d.b);
+    return size_t(lanes) * sizeof(float2) << maxb;
+}
 
 void jit_release(cudaLibrary_t lib) {
     if (lib) cudaLibraryUnload(lib);

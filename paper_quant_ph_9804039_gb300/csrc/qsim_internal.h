@@ -240,11 +240,13 @@ void jit_release(cudaLibrary_t lib);
 void jit_release(const std::vector<cudaLibrary_t> &libs);
 // The persistent trajectory kernel in register rounds ("qs_traj"): passes with
 // their rounds, op j of pass p = regops[passes[p].op_begin + j] whose gate is
-// trajectory op src[p][j]; __launch_bounds__(256, min_blocks).
+// trajectory op src[p][j]; `lanes` trajectories per CTA of 256 * lanes
+// threads, __launch_bounds__(256 * lanes, min_blocks).
 int jit_build_traj(int M, const std::vector<TilePassDesc> &passes, const std::vector<RegOp> &regops,
                    const std::vector<RoundDesc> &rounds, const std::vector<std::vector<int>> &src, int min_blocks,
-                   cudaLibrary_t *lib, cudaKernel_t *kernel, std::string *log);
+                   int lanes, cudaLibrary_t *lib, cudaKernel_t *kernel, std::string *log);
 size_t jit_pass_smem_bytes(const TilePassDesc &d);  // the two staged tiles of a specialised pass
+size_t jit_traj_smem_bytes(const std::vector<TilePassDesc> &passes, int lanes);  // two-lane tile buffers (0: static)
 int launch_jit_pass(cudaKernel_t k, void *dst, const void *src, int M, const TilePassDesc &d, const void *runs_dev,
                     cudaStream_t s);
 constexpr int kTileOpSmemBytes = 24 * 1024;  // a pass's ops are staged in shared memory up to this size

@@ -196,6 +196,7 @@ struct qsim_traj_plan {
     // register-round kernel generated for the circuit (kernel_kind 2)
     int kernel_kind = 1;  // 1: shared-memory tile kernel, 2: register rounds
     int per_sm = 2;       // resident trajectories per SM (register kernel)
+    int lanes = 1;        // trajectories per CTA of the register kernel (run in lockstep)
     cudaLibrary_t jit_lib = nullptr;
     cudaKernel_t jit_k = nullptr;
     std::string log;      // why the register kernel could not be built
@@ -323,8 +324,9 @@ int upload_tables(qsim_traj_plan *p) {
 int launch_traj(qsim_traj_plan *p, int T) {
     QS_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), p->stream));
     if (p->kernel_kind == 2) {
+        // one workspace per lane of each CTA: lanes * grid <= p->grid
         unsigned grid = unsigned(num_sms() * p->per_sm);
-        if (grid > unsigned(p->grid)) grid = unsigned(p->grid);
+        if (grid > unsigned(p->grid / p->lanes)) grid = unsigned(p->grid / p->lanes);
         const TrajOp *ops = p->d_ops;
         const double *eps = p->d_eps;
         int n = p->n;
@@ -333,7 +335,8 @@ int launch_traj(qsim_traj_plan *p, int T) {
         double *F = p->d_F;
         unsigned *counter = p->d_counter;
         void *args[] = {&ops, &eps, &n, &T, &ideal, &work, &F, &counter};
-        QS_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(p->jit_k), dim3(grid), dim3(256), args, 0, p->stream));
+        QS_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(p->jit_k), dim3(grid), dim3(256 * p->lanes), args,
+                                 p->smem, p->stream));
         return QSIM_OK;
     }
     k_trajectories<<<p->grid, kTrajThreads, p->smem, p->stream>>>(p->M, int(p->passes.size()), p->d_passes, p->d_ops,
@@ -348,11 +351,13 @@ int launch_traj(qsim_traj_plan *p, int T) {
 // into rounds by build_rounds, generated and compiled as one persistent
 // kernel.  Each op carries its trajectory op's index through the rounds in a
 // placeholder matrix entry (the kernel takes its matrices from shared memory).
-int build_register_kernel(qsim_traj_plan *p, const std::vector<Gate> &gates, const double *ax, int b) {
+// With lanes = 2 each CTA runs two trajectories in lockstep (one CTA per SM).
+int build_register_kernel(qsim_traj_plan *p, const std::vector<Gate> &gates, const double *ax, int b, int lanes) {
     if (p->jit_lib) jit_release(p->jit_lib);
     p->jit_lib = nullptr;
     p->jit_k = nullptr;
     p->kernel_kind = 1;
+    p->lanes = 1;
     if (p->M < b) return QSIM_EUNSUPPORTED;
     p->tile_bits = b;
     if (int rc = build_passes(p, gates, ax, b, 150)) return rc;
@@ -384,8 +389,12 @@ int build_register_kernel(qsim_traj_plan *p, const std::vector<Gate> &gates, con
         passes.push_back(d);
         src.push_back(s);
     }
-    if (int rc = jit_build_traj(p->M, passes, regops, rounds, src, 2, &p->jit_lib, &p->jit_k, &p->log)) return rc;
+    if (int rc = jit_build_traj(p->M, passes, regops, rounds, src, lanes > 1 ? 1 : 2, lanes, &p->jit_lib, &p->jit_k,
+                                &p->log))
+        return rc;
     p->kernel_kind = 2;
+    p->lanes = lanes;
+    p->smem = jit_traj_smem_bytes(passes, lanes);
     return QSIM_OK;
 }
 
@@ -488,14 +497,18 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
     }
     // configuration code: b (10..13) the shared-memory tile kernel with tiles
     // of 2^b; 100 + 10 b + s the register-round kernel with tiles of 2^b
-    // (b - 8 register qubits per thread) and s resident trajectories per SM
+    // (b - 8 register qubits per thread) and s = 1, 2 resident trajectories
+    // per SM, or s = 3: one CTA per SM running two trajectories in lockstep
     key.push_back(o.kernel);
     auto apply = [&](int code) -> int {
         if (code < 100) return set_tile_bits(p, gates, err_axis, code);
         const int b = (code - 100) / 10;
-        if (p->kernel_kind != 2 || p->tile_bits != b)
-            if (int r = build_register_kernel(p, gates, err_axis, b)) return r;
-        p->per_sm = code % 10;
+        int s = code % 10;
+        if (s == 3 && p->grid < 2) s = 1;  // a single workspace: one lane
+        const int lanes = s == 3 ? 2 : 1;
+        if (p->kernel_kind != 2 || p->tile_bits != b || p->lanes != lanes)
+            if (int r = build_register_kernel(p, gates, err_axis, b, lanes)) return r;
+        p->per_sm = s == 3 ? 1 : s;
         return QSIM_OK;
     };
     int best = 0;
@@ -529,7 +542,8 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
         if (o.kernel != 1)
             for (int b : {11, 12})
                 if (b <= M)
-                    for (int s : {1, 2}) cands.push_back(100 + 10 * b + s);
+                    for (int s : {1, 2, 3})
+                        if (s < 3 || p->grid >= 2) cands.push_back(100 + 10 * b + s);
         if (cands.empty()) cands.push_back(10);
         float best_ms = 1e30f;
         const int Tt = std::min(max_T, p->grid);
@@ -561,6 +575,10 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
             if (code < 100)
                 snprintf(line, sizeof line, "shared-memory kernel, tiles 2^%d: %.3f ms for %d trajectories\n", code, ms,
                          Tt);
+            else if (code % 10 == 3)
+                snprintf(line, sizeof line,
+                         "register kernel, tiles 2^%d, %d register qubits, 2 lanes per CTA: %.3f ms for %d trajectories\n",
+                         (code - 100) / 10, (code - 100) / 10 - kRegThreadBits, ms, Tt);
             else
                 snprintf(line, sizeof line,
                          "register kernel, tiles 2^%d, %d register qubits, %d per SM: %.3f ms for %d trajectories\n",
@@ -587,7 +605,7 @@ int qsim_traj_plan_create(int M, const qsim_gate *ideal, const double *err_axis,
         char line[160];
         snprintf(line, sizeof line, "chosen: %s, tiles 2^%d%s\n",
                  p->kernel_kind == 2 ? "register-round kernel" : "shared-memory tile kernel", p->tile_bits,
-                 p->kernel_kind == 2 ? (p->per_sm == 1 ? ", 1 per SM" : ", 2 per SM") : "");
+                 p->kernel_kind != 2 ? "" : p->lanes == 2 ? ", 2 lanes per CTA" : p->per_sm == 1 ? ", 1 per SM" : ", 2 per SM");
         p->tune += line;
     }
     *out = p;
