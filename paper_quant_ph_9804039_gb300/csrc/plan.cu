@@ -10,7 +10,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -66,6 +69,7 @@ struct qsim_plan {
     mutable bool last_absorbed = false;  // the last execution left the permutation pass to the gather
     std::string jit_log;
     std::string auto_log;  // the AUTO mode's estimates
+    std::string group_log;  // how the fused blocks were grouped
     int *d_status = nullptr;  // set by a kernel whose bounded wait ran out
     int fuse_k = 0;
     // non-null: device tables are allocated and freed stream-ordered on this
@@ -1100,7 +1104,38 @@ void block_rimg(const std::vector<double> &U, int k, __half *img) {
     }
 }
 
-FusedDesc fused_desc(int M, int k, const int *bq) {
+// Shared-memory wavefronts of the split warps' operand writes for skew
+// candidate (c, sh) of fused_desc at width k: they depend on the width only
+// (not on the block's qubits), so they are counted once per process.
+long operand_write_cost(int k, int c, int sh) {
+    struct Table {
+        long v[6][18][6];
+    };
+    static const Table table = [] {
+        Table t{};
+        for (int kk = 3; kk <= 5; ++kk) {
+            const int NA = 1 << kk, W = 4 * NA, NROWS = 1 << (kFusedTileBits - kk);
+            uint32_t sa[32];
+            for (int cc = 0; cc < 18; ++cc)
+                for (int s = 0; s < 6; ++s) {
+                    long cost = 0;
+                    for (int w = 0; w < 4; ++w)
+                        for (int st = 0; st < NA; ++st) {
+                            for (int l = 0; l < 32; ++l) {
+                                const int g = ((l * (cc == 0 ? 0 : 2 * cc - 1)) ^ (s ? (l >> s) : 0)) & (NA - 1);
+                                sa[l] = operand_offset(W, uint32_t(32 * w + l), 4u * uint32_t(st ^ g));
+                            }
+                            cost += 2 * wavefronts(sa, 4);
+                        }
+                    t.v[kk][cc][s] = cost * (NROWS / 128);
+                }
+        }
+        return t;
+    }();
+    return table.v[k][c][sh];
+}
+
+FusedDesc fused_desc_compute(int M, int k, const int *bq) {
     FusedDesc d{};
     d.k = k;
     const int nf = kFusedTileBits - k, NA = 1 << k, NROWS = 1 << nf, KR = 2 * NA, W = 2 * KR;
@@ -1157,21 +1192,20 @@ FusedDesc fused_desc(int M, int k, const int *bq) {
     // fewest shared-memory wavefronts over the warp's input reads and operand writes
     {
         long best = -1;
-        uint32_t la[32], sa[32];
+        uint32_t la[32];
         uint8_t g[32];
         for (int c = 0; c < 18; ++c)
             for (int sh = 0; sh < 6; ++sh) {
                 for (int l = 0; l < 32; ++l) g[l] = uint8_t(((l * (c == 0 ? 0 : 2 * c - 1)) ^ (sh ? (l >> sh) : 0)) & (NA - 1));
-                long cost = 0;
+                long cost = operand_write_cost(k, c, sh);
                 for (int w = 0; w < 4; ++w)
                     for (int rb = 0; rb < NROWS / 128; ++rb)
                         for (int st = 0; st < NA; ++st) {
                             for (int l = 0; l < 32; ++l) {
                                 const int rho = 32 * w + l, a = st ^ g[l];
                                 la[l] = 8u * (uint32_t(d.posA[a]) | d.posM[rb * 128 + rho]);
-                                sa[l] = operand_offset(W, uint32_t(rho), 4u * uint32_t(a));
                             }
-                            cost += wavefronts(la, 8) + 2 * wavefronts(sa, 4);
+                            cost += wavefronts(la, 8);
                         }
                 if (best < 0 || cost < best) {
                     best = cost;
@@ -1207,6 +1241,42 @@ FusedDesc fused_desc(int M, int k, const int *bq) {
     return d;
 }
 
+// fused_desc_compute is a pure function of (M, k, the block's qubits) that
+// takes milliseconds (the wavefront searches): its results are kept for the
+// process (at most kDescCacheMax of them), so the ideal and noisy circuits,
+// and every later plan over the same qubit sets, look them up.
+constexpr size_t kDescCacheMax = 4096;
+std::mutex g_desc_mu;
+std::map<std::pair<uint64_t, int>, FusedDesc> g_desc_cache;
+
+std::pair<uint64_t, int> desc_key(int M, int k, const int *bq) {
+    uint64_t B = 0;
+    for (int j = 0; j < k; ++j) B |= bit(bq[j]);
+    return {B, M * 8 + k};
+}
+
+bool desc_lookup(int M, int k, const int *bq, FusedDesc *d) {
+    std::lock_guard<std::mutex> lock(g_desc_mu);
+    auto it = g_desc_cache.find(desc_key(M, k, bq));
+    if (it == g_desc_cache.end()) return false;
+    *d = it->second;
+    return true;
+}
+
+void desc_store(int M, int k, const int *bq, const FusedDesc &d) {
+    std::lock_guard<std::mutex> lock(g_desc_mu);
+    if (g_desc_cache.size() >= kDescCacheMax) g_desc_cache.clear();
+    g_desc_cache[desc_key(M, k, bq)] = d;
+}
+
+FusedDesc fused_desc(int M, int k, const int *bq) {
+    FusedDesc d;
+    if (desc_lookup(M, k, bq, &d)) return d;
+    d = fused_desc_compute(M, k, bq);
+    desc_store(M, k, bq, d);
+    return d;
+}
+
 // Grouping into blocks of k qubits (every qubit of a gate, controls
 // included, belongs to the block).  A gate may join a block ahead of earlier
 // gates left for later blocks only if it commutes with each of them: neither
@@ -1214,7 +1284,8 @@ FusedDesc fused_desc(int M, int k, const int *bq) {
 // candidates are the greedy set (gates taken in order while their qubits fit,
 // padded to k with the lowest free qubits) and every window of k consecutive
 // qubits; the candidate that takes the most remaining gates wins (on the
-// 33-qubit brickwork: 75 blocks per circuit instead of the greedy 108).
+// 33-qubit brickwork: 75 blocks per circuit instead of the greedy 108;
+// fused_groups_beam below searches further).
 struct FusedGroup {
     uint64_t Q;
     std::vector<int> take;
@@ -1276,10 +1347,203 @@ std::vector<FusedGroup> fused_groups(const std::vector<Gate> &gates, int k, int 
     return out;
 }
 
-void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg) {
+// Beam search over the same candidates (every window of k consecutive
+// qubits, and the greedy set): at each depth every kept partial grouping is
+// extended by every candidate, extensions that leave the same gates are
+// merged, and the `width` best by (cost so far + the remaining gates, a
+// controlled gate counting 3, over 16) are kept.  A block costs 1, or
+// staged_cost when it holds qubit 0 or 1 (those blocks store through the
+// staging tile and run slower).  The cheaper of the beam's grouping and
+// fused_groups' is returned (on the 33-qubit brickwork with 24 layers:
+// 71 blocks, 7 of them staged, against 75 and 10).
+// fn(t) for t in [0, nt) on threads; whatever cannot get a thread runs here.
+template <class F>
+void run_parallel(size_t nt, F fn) {
+    std::vector<std::thread> pool;
+    size_t started = 0;
+    try {
+        for (; started < nt; ++started) pool.emplace_back(fn, started);
+    } catch (...) {
+    }
+    for (size_t t = started; t < nt; ++t) fn(t);
+    for (std::thread &th : pool) th.join();
+}
+
+double grouping_cost(const std::vector<FusedGroup> &g, double staged_cost) {
+    double c = 0;
+    for (const FusedGroup &x : g) c += (x.Q & 3u) ? staged_cost : 1.0;
+    return c;
+}
+
+std::vector<FusedGroup> fused_groups_beam(const std::vector<Gate> &gates, int k, int M, int width,
+                                          double staged_cost) {
+    std::vector<FusedGroup> base = fused_groups(gates, k, M);
+    if (width < 2 || gates.empty()) return base;
+    const size_t n = gates.size();
+    std::vector<uint64_t> gN(n), gA(n);
+    std::vector<int> gw(n);
+    for (size_t i = 0; i < n; ++i) {
+        gN[i] = gates[i].nondiag() ? bit(gates[i].t) : 0;
+        gA[i] = bit(gates[i].t) | gates[i].cmask;
+        gw[i] = gates[i].nc > 0 ? 3 : 1;
+    }
+    struct State {
+        double cost;
+        std::vector<int> rem;
+        std::vector<FusedGroup> hist;
+    };
+    struct Child {
+        double cost, score;
+        int parent;
+        uint64_t Q, hash;
+        size_t ntake;
+    };
+    // one candidate block Q on a state's remaining gates: its cost, score and
+    // a hash of the gates it leaves (materialised only for the kept children)
+    auto scan = [&](const State &st, int parent, uint64_t Q) {
+        uint64_t defN = 0, defA = 0, h = 1469598103934665603ull;
+        long wsum = 0;
+        size_t ntake = 0;
+        for (int gi : st.rem) {
+            const uint64_t N = gN[size_t(gi)], A = gA[size_t(gi)];
+            if (!((N & defA) || (A & defN)) && !(A & ~Q)) {
+                ++ntake;
+            } else {
+                defN |= N;
+                defA |= A;
+                wsum += gw[size_t(gi)];
+                h = (h ^ uint64_t(gi)) * 1099511628211ull;
+            }
+        }
+        Child c;
+        c.parent = parent;
+        c.Q = Q;
+        c.ntake = ntake;
+        c.hash = h ^ uint64_t(st.rem.size() - ntake);
+        c.cost = st.cost + ((Q & 3u) ? staged_cost : 1.0);
+        c.score = c.cost + double(wsum) / 16.0;
+        return c;
+    };
+    auto materialise = [&](const State &st, uint64_t Q, std::vector<int> &take, std::vector<int> &keep) {
+        uint64_t defN = 0, defA = 0;
+        for (int gi : st.rem) {
+            const uint64_t N = gN[size_t(gi)], A = gA[size_t(gi)];
+            if (!((N & defA) || (A & defN)) && !(A & ~Q)) {
+                take.push_back(gi);
+            } else {
+                keep.push_back(gi);
+                defN |= N;
+                defA |= A;
+            }
+        }
+    };
+    std::vector<uint64_t> windows;
+    for (int s0 = 0; s0 + k <= M; ++s0) windows.push_back(((uint64_t(1) << k) - 1) << s0);
+    auto greedy_set = [&](const State &st) {  // the greedy set, padded with the lowest free qubits
+        uint64_t defN = 0, defA = 0, Q = 0;
+        for (int gi : st.rem) {
+            const uint64_t N = gN[size_t(gi)], A = gA[size_t(gi)];
+            if (!((N & defA) || (A & defN)) && __builtin_popcountll(Q | A) <= k) {
+                Q |= A;
+            } else {
+                defN |= N;
+                defA |= A;
+            }
+        }
+        for (int q = 0; q < M && __builtin_popcountll(Q) < k; ++q) Q |= bit(q);
+        return Q;
+    };
+    std::vector<State> beam(1);
+    beam[0].cost = 0;
+    beam[0].rem.resize(n);
+    for (size_t i = 0; i < n; ++i) beam[0].rem[i] = int(i);
+    std::vector<Child> all;
+    for (size_t depth = 0; depth <= n; ++depth) {
+        all.clear();
+        for (size_t b = 0; b < beam.size(); ++b) {
+            const uint64_t G = greedy_set(beam[b]);
+            for (uint64_t Q : windows) {
+                Child c = scan(beam[b], int(b), Q);
+                if (c.ntake) all.push_back(c);
+            }
+            if (std::find(windows.begin(), windows.end(), G) == windows.end()) {
+                Child c = scan(beam[b], int(b), G);
+                if (c.ntake) all.push_back(c);
+            }
+        }
+        if (all.empty()) return base;  // cannot happen: a gate's own qubits take it
+        // a finished grouping ends the search: the cheapest one at this depth
+        const Child *done = nullptr;
+        for (const Child &c : all)
+            if (c.ntake == beam[size_t(c.parent)].rem.size() && (!done || c.cost < done->cost)) done = &c;
+        if (done) {
+            std::vector<FusedGroup> out = beam[size_t(done->parent)].hist;
+            out.push_back({done->Q, beam[size_t(done->parent)].rem});
+            return grouping_cost(out, staged_cost) < grouping_cost(base, staged_cost) ? out : base;
+        }
+        std::sort(all.begin(), all.end(), [](const Child &a, const Child &b) {
+            return a.score < b.score || (a.score == b.score && a.hash < b.hash);
+        });
+        std::vector<State> next;
+        std::vector<uint64_t> seen;
+        for (const Child &c : all) {
+            if (int(next.size()) >= width) break;
+            if (std::find(seen.begin(), seen.end(), c.hash) != seen.end()) continue;  // same gates left
+            seen.push_back(c.hash);
+            const State &par = beam[size_t(c.parent)];
+            State st;
+            st.cost = c.cost;
+            st.hist = par.hist;
+            FusedGroup grp{c.Q, {}};
+            materialise(par, c.Q, grp.take, st.rem);
+            st.hist.push_back(std::move(grp));
+            next.push_back(std::move(st));
+        }
+        beam.swap(next);
+    }
+    return base;
+}
+
+// Beam width of the fused grouping: the search pays off when a block pass
+// is long (2^28 amplitudes and more: a block saved is ~0.3 ms or more).
+constexpr int kBeamMinBits = 28;
+constexpr int kBeamWidth = 8;
+constexpr double kStagedCost = 1.25;  // staged / direct time of a block (measured 4.9 vs 6.1 TB/s)
+
+void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg, double staged_cost = kStagedCost) {
     const int M = p->M;
     const size_t per = fused_rimg_halves(k);
-    for (const FusedGroup &grp : fused_groups(p->gates, k, M)) {
+    const std::vector<FusedGroup> groups = M >= kBeamMinBits
+                                               ? fused_groups_beam(p->gates, k, M, kBeamWidth, staged_cost)
+                                               : fused_groups(p->gates, k, M);
+    {
+        int staged = 0;
+        for (const FusedGroup &g : groups) staged += (g.Q & 3u) ? 1 : 0;
+        char line[160];
+        std::snprintf(line, sizeof line, "grouping: %s (width %d), %zu blocks (%d holding qubit 0 or 1, staged cost %.2f)",
+                      M >= kBeamMinBits ? "beam search" : "windows and greedy", M >= kBeamMinBits ? kBeamWidth : 1,
+                      groups.size(), staged, staged_cost);
+        p->group_log = line;
+    }
+    // the blocks' descriptors not yet known to the process, computed in parallel
+    {
+        std::vector<std::vector<int>> missing;
+        std::vector<uint64_t> seen;
+        for (const FusedGroup &grp : groups) {
+            std::vector<int> bq;
+            for (int q = 0; q < M; ++q)
+                if (grp.Q & bit(q)) bq.push_back(q);
+            FusedDesc d;
+            if (std::find(seen.begin(), seen.end(), grp.Q) != seen.end() || desc_lookup(M, k, bq.data(), &d)) continue;
+            seen.push_back(grp.Q);
+            missing.push_back(bq);
+        }
+        const size_t nt = std::min<size_t>(missing.size(), 8);
+        run_parallel(nt, [&](size_t t) {
+            for (size_t i = t; i < missing.size(); i += nt) fused_desc(M, k, missing[i].data());
+        });
+    }
+    for (const FusedGroup &grp : groups) {
         const uint64_t Q = grp.Q;
         const std::vector<int> &take = grp.take;
         int bq[8], nb = 0;
@@ -1719,6 +1983,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
     }
     int mode = o.mode == QSIM_MODE_AUTO ? QSIM_MODE_TILED : o.mode;
     int auto_b = 0, auto_k = 0;
+    double staged_cost = kStagedCost;  // the measured ratio where AUTO has the rates
     if (o.mode == QSIM_MODE_AUTO && prec == QSIM_C64 && M >= 20) {
         // the candidates (tile passes of 2^12 or 2^11 amplitudes, fused blocks
         // of width 5, 4 or 3, unless opts fix them) planned on the host and
@@ -1775,6 +2040,8 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
                 mode = QSIM_MODE_FUSED;
                 auto_k = k;
                 auto_b = 0;
+                if (rates.fused_staged[k] > 0 && rates.fused_direct[k] > 0)
+                    staged_cost = rates.fused_direct[k] / rates.fused_staged[k];
             }
         }
         std::snprintf(line, sizeof line, " chosen %s %d; rates %s", mode == QSIM_MODE_FUSED ? "fused k=" : "tiled b=",
@@ -1804,7 +2071,7 @@ int plan_create_on(int M, qsim_prec prec, const qsim_gate *gates, size_t n, cons
     if (mode == QSIM_MODE_FUSED) {
         p->fuse_k = k_eff;
         std::vector<__half> rimg;
-        plan_fused(p, k_eff, rimg);
+        plan_fused(p, k_eff, rimg, staged_cost);
         int rc = fused_prepare();
         if (rc == QSIM_OK) rc = upload(p, &p->d_rimg, rimg.data(), rimg.size() * sizeof(__half), &p->rimg_bytes);
         if (rc) {
@@ -2082,6 +2349,7 @@ int qsim_plan_describe(const qsim_plan *p, char *buf, int64_t len, int64_t *need
     }
     if (!p->jit_log.empty()) add("specialisation: %s\n", p->jit_log.c_str());
     if (!p->auto_log.empty()) add("%s\n", p->auto_log.c_str());
+    if (!p->group_log.empty()) add("%s\n", p->group_log.c_str());
     for (size_t j = 0; j < p->steps.size(); ++j) {
         const Step &st = p->steps[j];
         if (st.type == S_GATE) {

@@ -271,14 +271,15 @@ def test_deferred_hadamard_scale_mid_plan(orc, M, specialize):
         assert np.array_equal(ref.get(), got)
 
 
-# ------------------------------------------ the brickwork workload at M=26
-@pytest.mark.parametrize("mode", ["fused", "tiled"])
-def test_brickwork_toffoli_m26(orc, mode):
+# ------------------------------------- the brickwork workload at M=26 and 28
+@pytest.mark.parametrize("M,mode", [(26, "fused"), (26, "tiled"), (28, "fused")])
+def test_brickwork_toffoli(orc, M, mode):
     """The 24-layer brickwork with a Toffoli after every 4th layer (over-
     rotation sigma=1e-3), from |0...0>, in place, as the benchmark runs it at
-    M=33: ideal and noisy states, F and norm against the oracle at M=26."""
-    _need_host(8)
-    M = 26
+    M=33: ideal and noisy states, F and norm against the oracle at M=26, and
+    at M=28, where the fused grouping is the beam search the benchmark's
+    plans use."""
+    _need_host(8 if M <= 26 else 32)
     c = W.circuit_c4_brickwork_toffoli(M, layers=24, sigma=1e-3)
     spec = mode == "tiled"
     ideal = qs.State(M)
@@ -287,6 +288,8 @@ def test_brickwork_toffoli_m26(orc, mode):
     p_n = qs.Plan(M, c["noisy"], mode=mode, specialize=spec)
     if spec:
         assert "specialised" in p_n.describe()
+    if M >= 28 and mode == "fused":  # the window grouping alone makes 66 blocks here
+        assert p_n.stats()["n_blocks"] < 66, p_n.stats()["n_blocks"]
     p_i.execute(ideal)
     p_n.execute(noisy)
     p_n.status()
