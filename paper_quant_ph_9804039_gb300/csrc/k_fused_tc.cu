@@ -50,11 +50,12 @@
 //                the canonical K-major swizzled layout the MMA reads;
 //   warps 8..11  epilogue: each thread reads its row of the accumulator
 //                (tcgen05.ld), removes the scale, renormalises and stores
-//                the amplitudes: straight to device memory when the 32 rows
-//                of a warp are 32 consecutive amplitudes (the block avoids
-//                qubits 0..4; then a fourth input stage takes the staging
-//                tile's shared memory), otherwise into an XOR-swizzled
-//                staging tile that the four warps copy out in coalesced runs.
+//                the amplitudes: straight to device memory when a warp's
+//                stores fill whole 32-byte sectors (the block avoids qubits 0
+//                and 1; then a fourth input stage takes the staging tile's
+//                shared memory), otherwise into an XOR-swizzled staging tile
+//                of which each warp copies out its own quarter in 16-byte
+//                pieces (no barrier between the four warps).
 // The split warps release an input stage as soon as the tile is in their
 // registers, before converting it.
 // Every mbarrier wait is bounded: the main loops' waits by wait_ns (2 s by
@@ -251,7 +252,6 @@ struct SmemCtl {
     uint64_t full_a[kNA], empty_a[kNA];
     uint64_t full_acc[kNA], empty_acc[kNA];
     uint64_t bar_r;
-    uint64_t epi_full, epi_free;          // staging tile written / copied out (4 epilogue warps)
     uint64_t runoff[32];                  // device offset of run r of a tile (tile 0)
     uint64_t runoff2[32];                 // device offset of tile-local index 128 j (tile 0)
     uint64_t gA[32];                      // device offset of combination a (sub-vector 0, tile 0)
@@ -310,8 +310,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&ctl.empty_acc[b], 4);
         }
         mbar_init(&ctl.bar_r, 1);
-        mbar_init(&ctl.epi_full, 4);
-        mbar_init(&ctl.epi_free, 4);
         ctl.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -489,7 +487,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------------------ epilogue
         const int qd = warp & 3;  // TMEM lane quadrant of this warp
-        const int te = tid - kEpi0 * 32;  // 0..127
         const unsigned char *outb = sm + C::OFF_OUT;
         for (uint64_t i = 0; i < n_local; ++i) {
             const int t = int(i % kNA);
@@ -542,10 +539,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 continue;
             }
-            if (i > 0 && !warp_wait(&ctl.epi_free, uint32_t((i - 1) & 1), abort, wait_ns)) {  // staging copied out
-                ok = false;
-                break;
-            }
+            // staged: warp qd's rows fill the quarter of the staging tile whose
+            // tile bits b5, b6 (those of sub-vector bits 5 and 6) equal qd, and
+            // the warp copies that quarter out itself, so the four warps never
+            // wait for one another.  b5 and b6 are tile bits 6 and up (the block
+            // holds qubit 0 or 1, below them), so a quarter is made of runs of
+            // at least 64 amplitudes: 16-byte pieces, each warp store 512
+            // contiguous bytes.  The swizzle only mixes bits 0..3 with bits
+            // outsh..outsh+3, so it keeps every quarter and every aligned pair.
 #pragma unroll
             for (int rb = 0; rb < C::NRB; ++rb) {
                 const uint32_t swm = 8u * stg_swz(ctl.posM[rb * 128 + rho], d.outsh);
@@ -555,24 +556,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                         make_float2(y[rb][2 * a], y[rb][2 * a + 1]);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl.epi_full);
-            if (!warp_wait(&ctl.epi_full, uint32_t(i & 1), abort, wait_ns)) {
-                ok = false;
-                break;
+            {
+                const uint32_t b5 = ctl.posM[32], b6 = ctl.posM[64];
+                const uint32_t fixed = ((qd & 1) ? b5 : 0u) | ((qd & 2) ? b6 : 0u);
+#pragma unroll
+                for (int it0 = 0; it0 < 16; it0 += 8) {  // 8 loads in flight, then their stores
+                    float4 v[8];
+                    float4 *dp[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        uint32_t u = uint32_t((it0 + j) * 64 + 2 * lane);  // the quarter's index, b5 and b6 inserted
+                        u = ((u & ~(b5 - 1u)) << 1) | (u & (b5 - 1u));
+                        u = ((u & ~(b6 - 1u)) << 1) | (u & (b6 - 1u));
+                        u |= fixed;
+                        const uint32_t su = stg_swz(u, d.outsh);
+                        float4 w = *reinterpret_cast<const float4 *>(outb + 8u * (su & ~1u));
+                        if (su & 1u) w = make_float4(w.z, w.w, w.x, w.y);  // the pair stored swapped
+                        v[j] = w;
+                        dp[j] = reinterpret_cast<float4 *>(dst + base + ctl.runoff2[u >> 7] + (u & 127u));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) *dp[j] = v[j];
+                }
             }
-            const uint32_t swt = stg_swz(uint32_t(te), d.outsh);
-            float2 *dbase = dst + base + uint32_t(te);
-#pragma unroll
-            for (int j0 = 0; j0 < 32; j0 += 8) {  // 8 loads in flight, then their stores
-                float2 v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j)  // u = te + 128 j; staging index swz(u) = swz(te) ^ swz(128 j)
-                    v[j] = *reinterpret_cast<const float2 *>(outb + 8u * (swt ^ stg_swz(uint32_t(j0 + j) << 7, d.outsh)));
-#pragma unroll
-                for (int j = 0; j < 8; ++j) dbase[ctl.runoff2[j0 + j]] = v[j];
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl.epi_free);
+            __syncwarp();  // the quarter is read before the next tile's rows overwrite it
         }
         if (!ok) {
             if (lane == 0) atomicExch(status, QSIM_ETIMEOUT);

@@ -1214,7 +1214,9 @@ FusedDesc fused_desc_compute(int M, int k, const int *bq) {
             }
     }
     // epilogue: thread = sub-vector row, writes combination a at swz(posA[a] | posM[m]);
-    // then the tile is read in index order; pick the staging swizzle shift
+    // then warp w reads back the quarter of the tile whose bits posM[32],
+    // posM[64] equal w, 16 bytes (an aligned pair) a lane; pick the staging
+    // swizzle shift
     {
         long best = -1;
         uint32_t ad[32];
@@ -1227,10 +1229,17 @@ FusedDesc fused_desc_compute(int M, int k, const int *bq) {
                         for (int l = 0; l < 32; ++l) ad[l] = 8u * swz(uint32_t(d.posA[a]) | d.posM[rb * 128 + 32 * w + l]);
                         cost += wavefronts(ad, 8);
                     }
+            const uint32_t b5 = d.posM[32], b6 = d.posM[64];
             for (int w = 0; w < 4; ++w)
-                for (int j = 0; j < 32; ++j) {
-                    for (int l = 0; l < 32; ++l) ad[l] = 8u * swz(uint32_t(32 * w + l + 128 * j));
-                    cost += wavefronts(ad, 8);
+                for (int it = 0; it < 16; ++it) {
+                    for (int l = 0; l < 32; ++l) {
+                        uint32_t u = uint32_t(it * 64 + 2 * l);
+                        u = ((u & ~(b5 - 1u)) << 1) | (u & (b5 - 1u));
+                        u = ((u & ~(b6 - 1u)) << 1) | (u & (b6 - 1u));
+                        u |= ((w & 1) ? b5 : 0u) | ((w & 2) ? b6 : 0u);
+                        ad[l] = 8u * (swz(u) & ~1u);
+                    }
+                    cost += wavefronts(ad, 16);
                 }
             if (best < 0 || cost < best) {
                 best = cost;
