@@ -1356,15 +1356,6 @@ std::vector<FusedGroup> fused_groups(const std::vector<Gate> &gates, int k, int 
     return out;
 }
 
-// Beam search over the same candidates (every window of k consecutive
-// qubits, and the greedy set): at each depth every kept partial grouping is
-// extended by every candidate, extensions that leave the same gates are
-// merged, and the `width` best by (cost so far + the remaining gates, a
-// controlled gate counting 3, over 16) are kept.  A block costs 1, or
-// staged_cost when it holds qubit 0 or 1 (those blocks store through the
-// staging tile and run slower).  The cheaper of the beam's grouping and
-// fused_groups' is returned (on the 33-qubit brickwork with 24 layers:
-// 71 blocks, 7 of them staged, against 75 and 10).
 // fn(t) for t in [0, nt) on threads; whatever cannot get a thread runs here.
 template <class F>
 void run_parallel(size_t nt, F fn) {
@@ -1378,15 +1369,26 @@ void run_parallel(size_t nt, F fn) {
     for (std::thread &th : pool) th.join();
 }
 
+// Beam search over the same candidates (every window of k consecutive
+// qubits, and the greedy set): at each depth every kept partial grouping is
+// extended by every candidate, extensions that leave the same gates are
+// merged, and the `width` best by (cost so far + the remaining gates, a
+// controlled gate counting 3, over 16) are kept.  A block costs 1, or
+// search_cost when it holds qubit 0 or 1 (those blocks store through the
+// staging tile and run slower).  The search is not monotone in its cost
+// weight, so fused_groups_beam runs it with three weights (1, the measured
+// staged/direct ratio, and their mean) and keeps the grouping with the lowest
+// cost at the measured ratio, or fused_groups' when that is cheaper (on the
+// 33-qubit brickwork with 24 layers: 70 blocks, 8 of them staged, against
+// 75 and 10).
 double grouping_cost(const std::vector<FusedGroup> &g, double staged_cost) {
     double c = 0;
     for (const FusedGroup &x : g) c += (x.Q & 3u) ? staged_cost : 1.0;
     return c;
 }
 
-std::vector<FusedGroup> fused_groups_beam(const std::vector<Gate> &gates, int k, int M, int width,
-                                          double staged_cost) {
-    std::vector<FusedGroup> base = fused_groups(gates, k, M);
+std::vector<FusedGroup> beam_search(const std::vector<Gate> &gates, int k, int M, int width, double staged_cost,
+                                    const std::vector<FusedGroup> &base) {
     if (width < 2 || gates.empty()) return base;
     const size_t n = gates.size();
     std::vector<uint64_t> gN(n), gA(n);
@@ -1513,11 +1515,23 @@ std::vector<FusedGroup> fused_groups_beam(const std::vector<Gate> &gates, int k,
     return base;
 }
 
+std::vector<FusedGroup> fused_groups_beam(const std::vector<Gate> &gates, int k, int M, int width,
+                                          double staged_cost) {
+    const std::vector<FusedGroup> base = fused_groups(gates, k, M);
+    const double weights[3] = {1.0, staged_cost, 0.5 * (1.0 + staged_cost)};
+    std::vector<FusedGroup> found[3];
+    run_parallel(3, [&](size_t i) { found[i] = beam_search(gates, k, M, width, weights[i], base); });
+    size_t best = 0;
+    for (size_t i = 1; i < 3; ++i)
+        if (grouping_cost(found[i], staged_cost) < grouping_cost(found[best], staged_cost)) best = i;
+    return grouping_cost(found[best], staged_cost) < grouping_cost(base, staged_cost) ? found[best] : base;
+}
+
 // Beam width of the fused grouping: the search pays off when a block pass
 // is long (2^28 amplitudes and more: a block saved is ~0.3 ms or more).
 constexpr int kBeamMinBits = 28;
 constexpr int kBeamWidth = 8;
-constexpr double kStagedCost = 1.25;  // staged / direct time of a block (measured 4.9 vs 6.1 TB/s)
+constexpr double kStagedCost = 1.30;  // staged / direct time of a block (measured 4.66 vs 6.04 TB/s, dense state)
 
 void plan_fused(qsim_plan *p, int k, std::vector<__half> &rimg, double staged_cost = kStagedCost) {
     const int M = p->M;
