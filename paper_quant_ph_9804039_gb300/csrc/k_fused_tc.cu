@@ -39,7 +39,9 @@
 // and pipelined over tiles:
 //   warps 0..2   producers: asynchronous copies of a tile into one of 3 or 4
 //                input stages, each lane arriving on the stage's mbarrier
-//                when its copies have landed;
+//                when its copies have landed (a lane's 16-byte pieces and
+//                their offsets from the tile's base are fixed per CTA and
+//                computed once: per tile the producers were issue-bound);
 //   warp 3       MMA: 12 tcgen05.mma per tile (3 products x row blocks x
 //                K steps of 16) into one of 2 TMEM accumulators (64 columns
 //                each), committed to mbarriers;
@@ -358,6 +360,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             bulk_g2s(Bs + bstride, rimg + C::B_BYTES / 2, C::B_BYTES, &ctl.bar_r);
         }
         const uint32_t rmask = run_amps - 1;
+        // this lane's 16-byte pieces of a tile (piece c = ptid + 96 j holds
+        // tile amplitudes 2c, 2c + 1): their byte offsets from the tile's base,
+        // the same for every tile, so they are computed once
+        constexpr int kPieces = (kTileAmps / 2 + 32 * kProd - 1) / (32 * kProd);
+        uint64_t poff[kPieces];
+#pragma unroll
+        for (int j = 0; j < kPieces; ++j) {
+            const int c = ptid + j * 32 * kProd;
+            const uint32_t u = 2u * uint32_t(c < kTileAmps / 2 ? c : 0);
+            poff[j] = 8u * (ctl.runoff[u >> d.runbits] + (u & rmask));
+        }
         for (uint64_t i = 0; i < n_local; ++i) {
             const int s = int(i % kNIn);
             if (i >= kNIn && !warp_wait(&ctl.empty_in[s], uint32_t(((i / kNIn) & 1) ^ 1), abort, wait_ns)) {
@@ -366,10 +379,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const uint64_t base = tile_base(i);
             unsigned char *buf = sm + C::OFF_IN + size_t(s) * kInBytes;
-#pragma unroll 4
-            for (int c = ptid; c < kTileAmps / 2; c += 32 * kProd) {
-                const uint32_t u = 2u * uint32_t(c);
-                cp_async16(buf + 8u * u, src + base + ctl.runoff[u >> d.runbits] + (u & rmask));
+            const unsigned char *srcb = reinterpret_cast<const unsigned char *>(src + base);
+#pragma unroll
+            for (int j = 0; j < kPieces; ++j) {
+                const int c = ptid + j * 32 * kProd;
+                if (j + 1 < kPieces || c < kTileAmps / 2) cp_async16(buf + 16u * uint32_t(c), srcb + poff[j]);
             }
             cp_async_arrive(&ctl.full_in[s]);
             issued = i + 1;
@@ -549,45 +563,45 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int a = 0; a < C::NA; ++a) drow[ctl.gA[a]] = make_float2(y[rb][2 * a], y[rb][2 * a + 1]);
                 }
-                continue;
-            }
-            // staged: warp qd's rows fill the quarter of the staging tile whose
-            // tile bits b5, b6 (those of sub-vector bits 5 and 6) equal qd, and
-            // the warp copies that quarter out itself, so the four warps never
-            // wait for one another.  b5 and b6 are tile bits 6 and up (the block
-            // holds qubit 0 or 1, below them), so a quarter is made of 16 pieces
-            // of 64 amplitudes: 16 bytes a lane, each warp store 512 contiguous
-            // bytes; the pieces' tile indices and device offsets are tabled once
-            // per CTA (computing them per tile cost a fifth of the staged
-            // blocks' speed).  The swizzle only mixes bits 0..3 with bits
-            // outsh..outsh+3, so it keeps every quarter and every aligned pair.
+            } else {
+                // staged: warp qd's rows fill the quarter of the staging tile whose
+                // tile bits b5, b6 (those of sub-vector bits 5 and 6) equal qd, and
+                // the warp copies that quarter out itself, so the four warps never
+                // wait for one another.  b5 and b6 are tile bits 6 and up (the block
+                // holds qubit 0 or 1, below them), so a quarter is made of 16 pieces
+                // of 64 amplitudes: 16 bytes a lane, each warp store 512 contiguous
+                // bytes; the pieces' tile indices and device offsets are tabled once
+                // per CTA (computing them per tile cost a fifth of the staged
+                // blocks' speed).  The swizzle only mixes bits 0..3 with bits
+                // outsh..outsh+3, so it keeps every quarter and every aligned pair.
 #pragma unroll
-            for (int rb = 0; rb < C::NRB; ++rb) {
-                const uint32_t swm = 8u * stg_swz(ctl.posM[rb * 128 + rho], d.outsh);
+                for (int rb = 0; rb < C::NRB; ++rb) {
+                    const uint32_t swm = 8u * stg_swz(ctl.posM[rb * 128 + rho], d.outsh);
 #pragma unroll
-                for (int a = 0; a < C::NA; ++a)
-                    *reinterpret_cast<float2 *>(const_cast<unsigned char *>(outb) + (ctl.swA8[a] ^ swm)) =
-                        make_float2(y[rb][2 * a], y[rb][2 * a + 1]);
-            }
-            __syncwarp();
-            {
-                float2 *dq = dst + base + 2 * lane;
-#pragma unroll
-                for (int it0 = 0; it0 < 16; it0 += 8) {  // 8 loads in flight, then their stores
-                    float4 v[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const uint32_t u = ctl.qidx[qd][it0 + j] | uint32_t(2 * lane);
-                        const uint32_t su = stg_swz(u, d.outsh);
-                        float4 w = *reinterpret_cast<const float4 *>(outb + 8u * (su & ~1u));
-                        if (su & 1u) w = make_float4(w.z, w.w, w.x, w.y);  // the pair stored swapped
-                        v[j] = w;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) *reinterpret_cast<float4 *>(dq + ctl.qdev[qd][it0 + j]) = v[j];
+                    for (int a = 0; a < C::NA; ++a)
+                        *reinterpret_cast<float2 *>(const_cast<unsigned char *>(outb) + (ctl.swA8[a] ^ swm)) =
+                            make_float2(y[rb][2 * a], y[rb][2 * a + 1]);
                 }
+                __syncwarp();
+                {
+                    float2 *dq = dst + base + 2 * lane;
+#pragma unroll
+                    for (int it0 = 0; it0 < 16; it0 += 8) {  // 8 loads in flight, then their stores
+                        float4 v[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const uint32_t u = ctl.qidx[qd][it0 + j] | uint32_t(2 * lane);
+                            const uint32_t su = stg_swz(u, d.outsh);
+                            float4 w = *reinterpret_cast<const float4 *>(outb + 8u * (su & ~1u));
+                            if (su & 1u) w = make_float4(w.z, w.w, w.x, w.y);  // the pair stored swapped
+                            v[j] = w;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) *reinterpret_cast<float4 *>(dq + ctl.qdev[qd][it0 + j]) = v[j];
+                    }
+                }
+                __syncwarp();  // the quarter is read before the next tile's rows overwrite it
             }
-            __syncwarp();  // the quarter is read before the next tile's rows overwrite it
         }
         if (!ok) {
             if (lane == 0) atomicExch(status, QSIM_ETIMEOUT);
