@@ -514,6 +514,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ epilogue
         const int qd = warp & 3;  // TMEM lane quadrant of this warp
         const unsigned char *outb = sm + C::OFF_OUT;
+        uint64_t rowoff[C::NRB];  // device offset of this thread's rows (direct stores), the same in every tile
+#pragma unroll
+        for (int rb = 0; rb < C::NRB; ++rb) {
+            const uint32_t u = ctl.posM[rb * 128 + 32 * qd + lane];
+            rowoff[rb] = ctl.runoff[u >> d.runbits] | (u & (run_amps - 1));
+        }
         for (uint64_t i = 0; i < n_local; ++i) {
             const int t = int(i % kNA);
             ok = warp_wait(&ctl.full_acc[t], uint32_t((i / kNA) & 1), abort, wait_ns);
@@ -558,8 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // of a combination a writes 256 contiguous bytes, no staging
 #pragma unroll
                 for (int rb = 0; rb < C::NRB; ++rb) {
-                    const uint32_t u = ctl.posM[rb * 128 + rho];
-                    float2 *drow = dst + base + (ctl.runoff[u >> d.runbits] | (u & (run_amps - 1)));
+                    float2 *drow = dst + base + rowoff[rb];
 #pragma unroll
                     for (int a = 0; a < C::NA; ++a) drow[ctl.gA[a]] = make_float2(y[rb][2 * a], y[rb][2 * a + 1]);
                 }
