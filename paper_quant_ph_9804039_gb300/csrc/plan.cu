@@ -1376,11 +1376,11 @@ void run_parallel(size_t nt, F fn) {
 // controlled gate counting 3, over 16) are kept.  A block costs 1, or
 // search_cost when it holds qubit 0 or 1 (those blocks store through the
 // staging tile and run slower).  The search is not monotone in its cost
-// weight, so fused_groups_beam runs it with three weights (1, the measured
-// staged/direct ratio, and their mean) and keeps the grouping with the lowest
-// cost at the measured ratio, or fused_groups' when that is cheaper (on the
-// 33-qubit brickwork with 24 layers: 70 blocks, 8 of them staged, against
-// 75 and 10).
+// weight, so fused_groups_beam runs it with six weights (1, the measured
+// staged/direct ratio, their mean, 1.15, 1.25 and 1.5) and keeps the grouping
+// with the lowest cost at the measured ratio, or fused_groups' when that is
+// cheaper (on the 33-qubit brickwork with 24 layers: 70 blocks, 8 of them
+// staged, against 75 and 10).
 double grouping_cost(const std::vector<FusedGroup> &g, double staged_cost) {
     double c = 0;
     for (const FusedGroup &x : g) c += (x.Q & 3u) ? staged_cost : 1.0;
@@ -1518,11 +1518,11 @@ std::vector<FusedGroup> beam_search(const std::vector<Gate> &gates, int k, int M
 std::vector<FusedGroup> fused_groups_beam(const std::vector<Gate> &gates, int k, int M, int width,
                                           double staged_cost) {
     const std::vector<FusedGroup> base = fused_groups(gates, k, M);
-    const double weights[3] = {1.0, staged_cost, 0.5 * (1.0 + staged_cost)};
-    std::vector<FusedGroup> found[3];
-    run_parallel(3, [&](size_t i) { found[i] = beam_search(gates, k, M, width, weights[i], base); });
+    const double weights[6] = {1.0, staged_cost, 0.5 * (1.0 + staged_cost), 1.15, 1.25, 1.5};
+    std::vector<FusedGroup> found[6];
+    run_parallel(6, [&](size_t i) { found[i] = beam_search(gates, k, M, width, weights[i], base); });
     size_t best = 0;
-    for (size_t i = 1; i < 3; ++i)
+    for (size_t i = 1; i < 6; ++i)
         if (grouping_cost(found[i], staged_cost) < grouping_cost(found[best], staged_cost)) best = i;
     return grouping_cost(found[best], staged_cost) < grouping_cost(base, staged_cost) ? found[best] : base;
 }
