@@ -10,8 +10,8 @@
 // triple index k = hi 3^t + lo maps to i = hi 3^(t+1) + lo, so consecutive
 // threads read consecutive amplitudes of each of the three slices (for
 // t = 0, three consecutive amplitudes each).  The divisions by powers of three
-// go through a double reciprocal with a one-step correction (exact for the
-// indices used, below 2^53).  Triples whose controls are not at their levels
+// go through a 64-bit multiply-high with a one-step correction (div_pow3,
+// exact for the indices used, below 2^40).  Triples whose controls are not at their levels
 // are neither read nor written.  complex64 uses the compensated (hi + lo)
 // matrix entries of the other kernels.
 #include <cmath>
